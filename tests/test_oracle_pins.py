@@ -1,0 +1,136 @@
+"""The FP64 oracle against what the paper and the mathematics fix.
+
+Eq. 11.12.24.1 (the 64-term blip expansion), Eq. 11.12.24.2 (the
+tensor-product basis, phi read as the centred cubic B-spline) and Eq. 7 (the
+stencil of 4 sites per direction) define the oracle; these pins check it
+without comparing it to itself.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pins
+
+
+def test_bspline_closed_forms():
+    assert pins.check_bspline_closed_forms() < 1e-15
+
+
+def test_bspline_continuity():
+    assert pins.check_bspline_continuity() < 1e-8
+
+
+def test_bspline_derivatives_match_fd():
+    assert pins.check_bspline_derivatives_fd() < 1e-9
+
+
+def test_partition_of_unity_and_zero_sum_derivatives():
+    assert pins.check_partition_of_unity() < 1e-13
+
+
+def test_cubic_polynomial_reproduction_triclinic():
+    assert pins.check_polynomial_reproduction() < 1e-12
+
+
+def test_plane_waves_interpolated_at_nodes_with_images():
+    assert pins.check_plane_wave_nodes() < 1e-12
+
+
+def test_finite_differences():
+    assert pins.check_finite_differences() < 1e-7
+
+
+def test_stencil_equals_bruteforce_on_tiny_grids():
+    assert pins.check_vs_bruteforce() < 1e-13
+
+
+def test_periodicity_and_grid_shift():
+    assert pins.check_translation() < 1e-12
+
+
+def test_golden_bspline_table():
+    """Exact rational values of B, B', B'' (tests/golden/bspline_values.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "bspline_values.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) >= 9
+    for x, b, db, d2b in rows:
+        from fractions import Fraction as F
+        assert oracle.B(float(F(x))) == pytest.approx(float(F(b)), abs=1e-16)
+        assert oracle.dB(float(F(x))) == pytest.approx(float(F(db)), abs=1e-16)
+        assert oracle.d2B(float(F(x))) == pytest.approx(float(F(d2b)), abs=1e-16)
+
+
+def test_nonfinite_position_gives_nan():
+    grid = (4, 4, 4)
+    tab = np.ones(grid + (2,))
+    pos = np.array([[np.nan, 0, 0], [0.1, 0.2, 0.3], [np.inf, 1, 1]])
+    v, g, l = oracle.eval_stencil(grid, np.eye(3) * 4, tab, pos)
+    assert np.isnan(v[0]).all() and np.isnan(v[2]).all() and np.isnan(l[0]).all()
+    assert np.allclose(v[1], 1.0)
+
+
+def test_thread_count_does_not_change_results():
+    grid = (6, 6, 6)
+    rng = np.random.default_rng(3)
+    tab = rng.normal(size=grid + (5,))
+    pos = rng.uniform(-5, 10, size=(37, 3))
+    a = oracle.eval_stencil(grid, pins.triclinic_lattice(), tab, pos, threads=1)
+    b = oracle.eval_stencil(grid, pins.triclinic_lattice(), tab, pos, threads=7)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_complex_table_splits_into_parts():
+    grid = (5, 6, 7)
+    rng = np.random.default_rng(4)
+    re = rng.normal(size=grid + (3,))
+    im = rng.normal(size=grid + (3,))
+    pos = rng.uniform(-3, 9, size=(11, 3))
+    lat = pins.triclinic_lattice()
+    vc, gc, lc = oracle.eval_stencil(grid, lat, re + 1j * im, pos)
+    vr, gr, lr = oracle.eval_stencil(grid, lat, re, pos)
+    vi, gi, li = oracle.eval_stencil(grid, lat, im, pos)
+    assert np.allclose(vc, vr + 1j * vi, atol=1e-14)
+    assert np.allclose(gc, gr + 1j * gi, atol=1e-13)
+    assert np.allclose(lc, lr + 1j * li, atol=1e-12)
+
+
+def test_absmag_bounds_outputs():
+    grid = (6, 5, 7)
+    rng = np.random.default_rng(5)
+    tab = rng.normal(size=grid + (4,))
+    pos = rng.uniform(-3, 9, size=(20, 3))
+    v, g, l, mag = oracle.eval_stencil(grid, pins.triclinic_lattice(), tab, pos, absmag=True)
+    assert (np.abs(v) <= mag[:, 0] + 1e-14).all()
+    for c in range(3):
+        assert (np.abs(g[:, c]) <= mag[:, 1 + c] + 1e-13).all()
+    assert (np.abs(l) <= mag[:, 4] + 1e-12).all()
+    # the value weights are non-negative B-spline products summing to 1
+    assert np.allclose(mag[:, 0], oracle.eval_stencil(grid, pins.triclinic_lattice(),
+                                                      np.abs(tab), pos)[0])
+
+
+def test_local_kinetic_closed_form():
+    """Orbitals with lap psi_l = -k_l^2 psi_l give T_L = 1/2 sum_sigma sum_l k_l^2."""
+    rng = np.random.default_rng(6)
+    n = 12
+    k2 = rng.uniform(0.5, 3.0, size=n)
+    vals = rng.normal(size=(2 * n, n))
+    laps = -vals * k2[None, :]
+    T, conds = oracle.kinetic.local_kinetic(vals, laps, [(0, n), (n, 2 * n)])
+    assert T == pytest.approx(0.5 * 2 * k2.sum(), rel=1e-12)
+    assert len(conds) == 2 and all(c >= 1 for c in conds)
+
+
+def test_local_kinetic_detects_swapped_index():
+    """A transposed Laplacian matrix changes T_L (so the index order is pinned)."""
+    rng = np.random.default_rng(7)
+    n = 8
+    vals = rng.normal(size=(n, n))
+    laps = rng.normal(size=(n, n))
+    T, _ = oracle.kinetic.local_kinetic(vals, laps, [(0, n)])
+    ref = -0.5 * sum(laps[j, l] * np.linalg.inv(vals)[l, j] for j in range(n) for l in range(n))
+    assert T == pytest.approx(ref, rel=1e-10)
+    Tt, _ = oracle.kinetic.local_kinetic(vals, laps.T, [(0, n)])
+    assert abs(Tt - T) > 1e-6
