@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark: orbital x electron evaluations per second (value + gradient +
+Laplacian) of the periodic cubic-blip path on GB300.
+
+Default workload: the TiO2-shaped table (tetragonal 17.4 x 17.4 x 11.2 bohr,
+72 x 72 x 48 grid, 768 real orbitals, FP32 storage) evaluated at 1,536
+uniform positions all at once (one batched launch per step).  A step is one
+blip_eval of the batch; L2 is flushed (512 MB write) between steps outside
+the per-step CUDA-event window.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import blip_inputs as bi  # noqa: E402
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the evaluation kernel on this workload, from ncu, keyed by the SHA-256 of
+# the kernel source it was measured on; reported as null once the kernel
+# changes.  Filled from the committed summary under profiles/.
+NCU_TRAFFIC = {
+}
+
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tio2",
+                    choices=["tio2", "tio2_batch", "tio2_precision", "cubic16"])
+    ap.add_argument("--batch", type=int, default=1536, help="electrons per walker (tio2_batch)")
+    ap.add_argument("--walkers", type=int, default=0, help="override walker count")
+    ap.add_argument("--storage", default="f32", choices=list(STORAGE))
+    ap.add_argument("--kernel", default="auto", help="auto | variant,chunks,warps,sort")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def make_workload(args, rank):
+    kw = {}
+    if args.workload == "tio2_batch":
+        kw["batch"] = args.batch
+    if args.walkers:
+        kw["n_walkers"] = args.walkers
+    w = bi.workload(args.workload, **kw)
+    w.pos_seed += 1000 * rank          # each rank evaluates its own walkers
+    return w
+
+
+def describe(w, args, E):
+    d = {"workload": f"{w.name}: cell {np.diag(w.lattice).tolist()} bohr, grid "
+                     f"{'x'.join(map(str, w.grid))}, {w.n_orb} "
+                     f"{'complex' if w.is_complex else 'real'} orbitals, {E} positions per step"
+                     + (f" ({w.n_walkers} walkers)" if w.n_walkers > 1 else " (all at once)"),
+         "electrons": E, "orbitals": w.n_orb, "storage": args.storage,
+         "l2": "flushed between steps (512 MB write, outside the event window)",
+         "positions": "uniform in cell" if w.uniform_n else "walker configs + N(0,0.3^2) moves"}
+    return d
+
+
+def touched_sites(grid, lattice, pos):
+    """Distinct grid sites whose coefficients a launch must read (the 4x4x4
+    stencils of all positions), for the compulsory-traffic model."""
+    n = np.array(grid)
+    ainv = np.linalg.inv(np.asarray(lattice, dtype=np.float64).T)
+    u = pos @ ainv.T
+    u -= np.floor(u)
+    u[u >= 1.0] = 0.0
+    base = np.floor(u * n).astype(np.int64) % n
+    mark = np.zeros(int(np.prod(n)), dtype=bool)
+    for kx in range(4):
+        ix = (base[:, 0] - 1 + kx) % n[0]
+        for ky in range(4):
+            iy = (base[:, 1] - 1 + ky) % n[1]
+            for kz in range(4):
+                iz = (base[:, 2] - 1 + kz) % n[2]
+                mark[(ix * n[1] + iy) * n[2] + iz] = True
+    return int(mark.sum())
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("blip_eval.cu", "blip_internal.h"):
+        with open(os.path.join(ROOT, "paper_1204_1121_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(w, tab, pos, seconds):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    E = len(pos)
+    t0 = time.perf_counter()
+    oracle.eval_stencil(w.grid, w.lattice, tab, pos[: min(E, 256)], threads=cores)
+    probe = time.perf_counter() - t0
+    per_e = probe / min(E, 256)
+    n = int(max(64, min(E, seconds / max(per_e, 1e-9))))
+    reps = max(1, int(seconds / max(per_e * n, 1e-9)))
+    reps = min(reps, 50)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.eval_stencil(w.grid, w.lattice, tab, pos[:n], threads=cores)
+    dt = time.perf_counter() - t0
+    Lr = w.n_orb
+    return {"value": n * reps * Lr / dt, "unit": "orbital*electron evals/s (val+grad+lap)",
+            "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of {E} positions x {reps} repeats, FP64, {cores} threads, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    import oracle
+    w = make_workload(args, 0)
+    tab = w.table()
+    pos, offs = w.positions()
+    cores = os.cpu_count() or 1
+    E = len(pos)
+    # bound each step to about 2 s of wall time
+    t0 = time.perf_counter()
+    oracle.eval_stencil(w.grid, w.lattice, tab, pos[: min(E, 256)], threads=cores)
+    per_e = (time.perf_counter() - t0) / min(E, 256)
+    n = int(max(16, min(E, 2.0 / max(per_e, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.eval_stencil(w.grid, w.lattice, tab, pos[:n], threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.eval_stencil(w.grid, w.lattice, tab, pos[:n], threads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = n * w.n_orb / (ms / 1e3)
+    unit = "orbital*electron evals/s (val+grad+lap)"
+    line = {"impl": "reference", "metric": "orbital*electron evals/s (val+grad+lap)",
+            "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(w, args, E),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": f"first {n} of {E} positions per step, FP64, {cores} threads"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1204_1121_gb300 as pb
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = make_workload(args, rank)
+    tab = w.table()
+    pos, offs = w.positions()
+    E = len(pos)
+    t = pb.BlipTable(w.grid, w.lattice, tab, storage=STORAGE[args.storage])
+    info = t.info()
+    dpos = torch.from_numpy(pos).cuda()
+    doffs = torch.from_numpy(offs).cuda()
+    out = t.alloc_outputs(E)
+    stream = torch.cuda.current_stream()
+    if args.kernel == "auto":
+        chosen = t.autotune(dpos, doffs, out=out)
+    else:
+        v_, c_, w_, s_ = (int(x) for x in args.kernel.split(","))
+        t.set_kernel(v_, c_, w_, s_)
+        chosen = (v_, c_, w_, s_)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        t.eval(dpos, doffs, out=out)
+
+    for k in range(max(3, args.warmup)):
+        flush.fill_(float(k))
+        step()
+    torch.cuda.synchronize()
+    st = t.status()
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - w0
+    clocks = sampler.stop()
+    per = [a.elapsed_time(b) for a, b in evs]
+    ms = statistics.mean(per)
+    if dist:
+        x = torch.tensor([ms], device="cuda")
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms = float(x.item())
+    evals = E * w.n_orb
+    value = world * evals / (ms / 1e3)
+
+    # roofline of the evaluation kernel (the only kernel in the step)
+    U = touched_sites(w.grid, w.lattice, pos)
+    Lr = info["Lreal"]
+    bytes_alg = U * Lr * ELEM_BYTES[args.storage] + 20 * Lr * E + 24 * E
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_alg / (ms / 1e3) / 1e9
+    kh = kernel_hash()
+    rec = NCU_TRAFFIC.get((kh, w.name, args.storage, E))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": rec,
+            "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
+            "algorithmic_bytes_per_launch": bytes_alg, "touched_sites": U,
+            "kernel_source_hash": kh,
+            "gather_model_GBps": (E * 64 * Lr * ELEM_BYTES[args.storage] + 20 * Lr * E) / (ms / 1e3) / 1e9,
+            "fp32_fma_per_launch": 320 * Lr * E}
+
+    line = {"metric": "orbital*electron evals/s (val+grad+lap)", "value": value,
+            "unit": "orbital*electron evals/s", "n_gpus": world, "steps": K,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": describe(w, args, E), "roofline": roof, "clocks": clocks,
+            "gpu_launches": K, "kernel_choice": list(chosen), "status": st,
+            "wall_s_timed_region": wall}
+
+    if not args.no_e2e:
+        # end to end through the host-buffer entry point: H2D positions,
+        # evaluation, D2H of all outputs, per step
+        hp = torch.from_numpy(pos).pin_memory()
+        ho = torch.from_numpy(offs).pin_memory()
+        hv = torch.empty((E, Lr), dtype=torch.float32).pin_memory()
+        hg = torch.empty((E, 3, Lr), dtype=torch.float32).pin_memory()
+        hl = torch.empty((E, Lr), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            t.eval_host(hp, ho, out=(hv, hg, hl))
+        tt = []
+        for _ in range(K):
+            t0 = time.perf_counter()
+            t.eval_host(hp, ho, out=(hv, hg, hl))
+            tt.append(time.perf_counter() - t0)
+        e_ms = 1e3 * statistics.mean(tt)
+        if dist:
+            x = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            e_ms = float(x.item())
+        line["e2e"] = {"value": world * evals / (e_ms / 1e3), "unit": "orbital*electron evals/s",
+                       "h2d_bytes_per_step": int(hp.numel() * 8 + ho.numel() * 4),
+                       "d2h_bytes_per_step": int((hv.numel() + hg.numel() + hl.numel()) * 4),
+                       "ms_per_step": e_ms, "api": "blip_eval_host (pinned host buffers)"}
+
+    if not args.no_extra and args.workload == "tio2" and rank == 0:
+        # one electron per launch (particle-by-particle order), 1,536 kernel
+        # nodes in one CUDA graph
+        o1 = t.alloc_outputs(E)
+        g = t.graph(dpos, o1, 1)
+        for _ in range(2):
+            g.launch()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record(stream)
+        for _ in range(reps):
+            g.launch()
+        b.record(stream)
+        torch.cuda.synchronize()
+        oms = a.elapsed_time(b) / reps
+        line["one_at_a_time"] = {"value": evals / (oms / 1e3), "ms_per_step": oms,
+                                 "us_per_electron": 1e3 * oms / E,
+                                 "how": "CUDA graph of 1,536 single-electron launches"}
+        g.close()
+
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, tab, pos, args.cpu_seconds)
+
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,207 @@
+/*
+ * blip.h - C ABI of libblip: periodic cubic-blip (B-spline) orbital
+ * evaluation on a GB300 (sm_103a) GPU.
+ *
+ * What it computes (Uejima & Maezono, arXiv:1204.1121, Sec. II.B,
+ * Eqs. 11.12.24.1, 11.12.24.2 and 7): for every electron position r_j and
+ * every orbital l of a precomputed coefficient table a[l, s~] on a periodic
+ * grid of n1 x n2 x n3 sites,
+ *
+ *     psi_l(r_j) = sum_{s=1}^{64} a_{l,s(r_j)} Theta_s(r_j),
+ *     Theta_s(r) = phi(g_1 - m_1) phi(g_2 - m_2) phi(g_3 - m_3),
+ *
+ * with g = diag(n) A^{-1} r the grid coordinates of r, A the matrix whose
+ * columns are the lattice vectors, site m at r = A diag(n)^{-1} m, phi the
+ * centred cubic B-spline (4 sites per direction, so s runs over 4^3 = 64
+ * sites per electron), and the coefficient of site m read at m mod n.  The
+ * library also returns the Cartesian gradient and Laplacian of every psi_l
+ * (chain rule: grad = J^T grad_g, lap = sum_ab (J J^T)_ab d_a d_b with
+ * J = diag(n) A^{-1}); these enter the local energy (Sec. II.B, step 4 of
+ * the Monte Carlo step).  Many electrons of many walkers are evaluated in one
+ * call, which is the batching the quasi-simultaneous update of Sec. IV.A
+ * (Eq. 11.12.23.1) makes possible: every trial move of a step is judged
+ * against the same frozen configuration, so all N x L evaluations are
+ * independent.
+ *
+ * Numerics: positions are wrapped into the cell and reduced to a cell index
+ * and an offset in FP64 on the GPU; weights and the 64-term contraction use
+ * FP32 with FP32 accumulation (the paper runs its GPU kernel in single
+ * precision, Sec. III.B and V.B).  Coefficients are stored as FP32, or as
+ * BF16 / FP16 with one FP32 scale per orbital.
+ *
+ * Conventions for every entry point:
+ *  - Return value: BLIP_OK (0) or a negative BLIP_ERR_* code; nothing is
+ *    thrown and no process state other than the table is changed.
+ *  - "device" pointers are CUDA global-memory addresses on the table's
+ *    device; "host" pointers are ordinary (pageable or pinned) memory.
+ *  - A stream is passed as void* (a cudaStream_t; NULL = the legacy default
+ *    stream).  Device work is asynchronous on that stream unless stated.
+ *  - The library never frees memory it did not allocate.
+ */
+#ifndef BLIP_H
+#define BLIP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define BLIP_OK                     0
+#define BLIP_ERR_INVALID_ARG       -1  /* NULL pointer, bad size or enum value   */
+#define BLIP_ERR_SINGULAR_LATTICE  -2  /* lattice vectors linearly dependent     */
+#define BLIP_ERR_OOM               -3  /* a device or host allocation failed     */
+#define BLIP_ERR_CUDA              -4  /* a CUDA call failed (see blip_last_cuda_error) */
+#define BLIP_ERR_UNSUPPORTED_DTYPE -5  /* storage kind not known                 */
+#define BLIP_ERR_NO_DEVICE         -6  /* no CUDA device, or not an sm_103 part  */
+
+/* ---- device-side status bits (reported by blip_status) ---------------- */
+#define BLIP_STATUS_NONFINITE_POS  0x1 /* a position was NaN/Inf: its outputs are NaN    */
+#define BLIP_STATUS_FAR_POS        0x2 /* |fractional coordinate| > 2^40: precision lost */
+#define BLIP_STATUS_BAD_OFFSETS    0x4 /* walker offsets not monotone or out of range    */
+#define BLIP_STATUS_TIMEOUT        0x8 /* a bounded wait in a kernel gave up             */
+
+/* ---- storage kinds ---------------------------------------------------- */
+typedef enum {
+    BLIP_F32 = 0,       /* real orbitals, FP32 coefficients                          */
+    BLIP_BF16 = 1,      /* real orbitals, BF16 coefficients x FP32 per-orbital scale */
+    BLIP_F16 = 2,       /* real orbitals, FP16 coefficients x FP32 per-orbital scale */
+    BLIP_C64 = 3,       /* complex orbitals, FP32 real/imaginary parts               */
+    BLIP_BF16PAIR = 4   /* complex orbitals, BF16 real/imaginary parts x FP32 scale  */
+} blip_dtype;
+
+/* ---- normalisation of the 1-D factor phi ------------------------------ */
+typedef enum {
+    BLIP_NORM_BSPLINE = 0,     /* phi = cubic B-spline, phi(0) = 2/3, sum over sites = 1 */
+    BLIP_NORM_ALFE_GILLAN = 1  /* phi = 3/2 x cubic B-spline, phi(0) = 1                  */
+} blip_norm;
+
+typedef struct blip_table_s *blip_table;
+typedef struct blip_graph_s *blip_graph;
+
+/*
+ * blip_create - build a device-resident coefficient table.
+ *
+ * Defines the table a~_{l,s~} of Eq. 7 (precomputed, read once at start-up,
+ * Sec. II.B) on the current CUDA device.
+ *   grid[3]           n1, n2, n3 >= 4: sites along lattice vectors a_1, a_2, a_3
+ *   lattice[9]        row i = lattice vector a_i in bohr (lattice[3*i + c])
+ *   n_orb             orbitals (complex orbitals for BLIP_C64 / BLIP_BF16PAIR), >= 1
+ *   storage           a blip_dtype
+ *   norm              a blip_norm
+ *   coeffs            layout [n1][n2][n3][n_orb], orbital index fastest; complex
+ *                     kinds interleave (re, im) per orbital.  Element type is
+ *                     double if coeffs_is_double, else float.
+ *   coeffs_on_device  0: coeffs is a host pointer; 1: a device pointer
+ *   out               receives the handle
+ * Ownership: the library copies (and converts / quantises) the coefficients
+ * into memory it owns; the caller keeps and frees its buffer.  The call
+ * synchronises the device before returning.  Errors: INVALID_ARG,
+ * SINGULAR_LATTICE, UNSUPPORTED_DTYPE, OOM, CUDA, NO_DEVICE; *out is NULL on
+ * error.
+ */
+int blip_create(const int grid[3], const double lattice[9], int n_orb, int storage, int norm,
+                const void *coeffs, int coeffs_is_double, int coeffs_on_device,
+                blip_table *out);
+
+/*
+ * blip_eval - values, gradients and Laplacians of all orbitals at a batch of
+ * positions (Eq. 11.12.24.1 for every (j, l); Sec. IV.A batching).
+ *   pos              device [n_elec][3] FP64 Cartesian positions (bohr), any
+ *                    finite values (they are wrapped into the cell)
+ *   n_elec           >= 0 (0 is a no-op)
+ *   walker_offsets   device [n_walkers + 1] int32 prefix offsets of the walkers'
+ *                    electrons in pos (offsets[0] = 0, offsets[n_walkers] =
+ *                    n_elec, non-decreasing), or NULL for one walker.  Checked
+ *                    on the device (BLIP_STATUS_BAD_OFFSETS).
+ *   values           device [n_elec][n_orb] float (complex kinds: float2)
+ *   grads            device [n_elec][3][n_orb] float (float2), or NULL
+ *   laps             device [n_elec][n_orb] float (float2), or NULL
+ *                    grads and laps must be both NULL (values-only mode) or
+ *                    both non-NULL.
+ *   stream           cudaStream_t
+ * No host synchronisation and no allocation on the steady path (scratch for
+ * the optional spatial sort is grown on the first call that needs it).
+ * Output buffers must not overlap each other or pos.  Errors: INVALID_ARG,
+ * CUDA.  Device-side problems are reported through blip_status.
+ */
+int blip_eval(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+              int n_walkers, void *values, void *grads, void *laps, void *stream);
+
+/*
+ * blip_eval_host - blip_eval with HOST buffers: copies pos (and offsets) to
+ * the device, evaluates, copies the outputs back, and synchronises.  Staging
+ * buffers are owned by the table and grown as needed.  Same layouts and
+ * errors as blip_eval; grads/laps may be NULL together.
+ */
+int blip_eval_host(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+                   int n_walkers, void *values, void *grads, void *laps);
+
+/*
+ * blip_status - synchronise the table's last stream and return (and clear)
+ * the OR of the device status bits raised since the last call.
+ */
+int blip_status(blip_table t, int *device_status);
+
+/* blip_destroy - free the table and everything it owns (NULL is accepted). */
+int blip_destroy(blip_table t);
+
+/* blip_strerror - static description of an error code. */
+const char *blip_strerror(int code);
+
+/* blip_last_cuda_error - the cudaError_t behind the last BLIP_ERR_CUDA. */
+int blip_last_cuda_error(void);
+
+/*
+ * blip_info - table facts for callers and benchmarks.
+ *   out[0] rows stored (n1 * n2 * (n3 + 3): three ghost planes along a_3)
+ *   out[1] stored row length in elements (orbital count padded)
+ *   out[2] real orbital components per row (n_orb, or 2 n_orb if complex)
+ *   out[3] bytes per stored element
+ *   out[4] table bytes on the device
+ *   out[5] storage kind, out[6] SM count, out[7] kernel variant in use
+ */
+int blip_info(blip_table t, long long out[8]);
+
+/*
+ * blip_set_kernel - choose the evaluation kernel and its tile shape.
+ *   variant    0: automatic (tuned choice); 1: register gather (each lane
+ *              loads its orbitals' coefficients straight into registers);
+ *              2: bulk-copy staging (one lane per warp streams the 4
+ *              contiguous z-rows of each stencil column into shared memory
+ *              with cp.async.bulk, other lanes consume them)
+ *   chunks     orbital chunks of 32 lanes x (16 bytes / element size) that
+ *              one warp evaluates per electron (1, 2, 3 or 6)
+ *   warps      warps per block (1..16)
+ *   sort       0: electrons in input order; 1: sort by grid cell first (L2
+ *              reuse for large batches)
+ * Errors: INVALID_ARG for values outside those sets.
+ */
+int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort);
+
+/*
+ * blip_autotune - time each kernel configuration on this batch shape and keep
+ * the fastest for batches of this size class.  Same arguments as blip_eval
+ * (the outputs are overwritten).  Synchronises the stream; must not be called
+ * during stream capture.  *chosen receives {variant, chunks, warps, sort}.
+ */
+int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+                  int n_walkers, void *values, void *grads, void *laps, void *stream,
+                  int chosen[4]);
+
+/*
+ * blip_graph_create - capture a fixed evaluation into a CUDA graph.
+ * The graph evaluates pos[0 .. n_elec) with the given buffers in launches of
+ * per_launch electrons each (per_launch = 1 reproduces one-at-a-time,
+ * particle-by-particle evaluation; per_launch = n_elec one batched launch).
+ * The pointers are baked into the graph and must stay valid.
+ */
+int blip_graph_create(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+                      int n_walkers, void *values, void *grads, void *laps, int per_launch,
+                      blip_graph *out);
+int blip_graph_launch(blip_graph g, void *stream);
+int blip_graph_destroy(blip_graph g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLIP_H */

@@ -1,0 +1,557 @@
+// C ABI of libblip (declared in include/blip.h): table lifetime, evaluation
+// entry points, status word, kernel choice, autotuning and CUDA graphs.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "blip_internal.h"
+#include "../../include/blip.h"
+
+using namespace blip;
+
+namespace {
+
+int g_last_cuda_error = 0;
+
+struct KernelChoice {
+    int variant, chunks, warps, sort;
+};
+
+}  // namespace
+
+struct blip_table_s {
+    int device = 0;
+    int sm_count = 0;
+    int grid[3] = {0, 0, 0};
+    int n_orb = 0, storage = 0, norm = 0, is_complex = 0;
+    int elem = ELEM_F32;
+    int Lreal = 0;
+    int nchunk = 0;
+    long long row_stride = 0;
+    long long rows = 0;
+    void *d_table = nullptr;
+    size_t table_bytes = 0;
+    float *d_scales = nullptr;
+    int *d_status = nullptr;
+    Geometry geo{};
+    KernelChoice choice{VAR_REGISTER, 1, 8, 0};
+    bool auto_mode = false;
+    std::map<int, KernelChoice> tuned;   // by batch size class (bit length of n_elec)
+    cudaStream_t last_stream = nullptr;
+    bool used = false;
+    // host-buffer entry point staging
+    cudaStream_t own_stream = nullptr;
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+struct blip_graph_s {
+    blip_table_s *table = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda_error = (int)e;
+    return e == cudaErrorMemoryAllocation ? BLIP_ERR_OOM : BLIP_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+// A with the lattice vectors as columns: A[c][i] = lattice[3 i + c].
+// Fills geo.ainv (row-major A^{-1}), J = diag(n) A^{-1}, M = J J^T.
+int make_geometry(const int grid[3], const double lattice[9], int norm, Geometry &geo)
+{
+    double A[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) A[c][i] = lattice[3 * i + c];
+    // inverse by Gauss-Jordan elimination with partial pivoting
+    double m[3][6];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 6; ++c) m[r][c] = c < 3 ? A[r][c] : (c - 3 == r ? 1.0 : 0.0);
+    double scale = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double nn = 0.0;
+        for (int c = 0; c < 3; ++c) nn += lattice[3 * i + c] * lattice[3 * i + c];
+        scale = std::max(scale, sqrt(nn));
+    }
+    if (!(scale > 0.0) || !isfinite(scale)) return BLIP_ERR_SINGULAR_LATTICE;
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 3; ++r)
+            if (fabs(m[r][col]) > fabs(m[piv][col])) piv = r;
+        if (fabs(m[piv][col]) <= 1e-12 * scale) return BLIP_ERR_SINGULAR_LATTICE;
+        if (piv != col)
+            for (int c = 0; c < 6; ++c) std::swap(m[piv][c], m[col][c]);
+        const double d = m[col][col];
+        for (int c = 0; c < 6; ++c) m[col][c] /= d;
+        for (int r = 0; r < 3; ++r) {
+            if (r == col) continue;
+            const double f = m[r][col];
+            for (int c = 0; c < 6; ++c) m[r][c] -= f * m[col][c];
+        }
+    }
+    double J[3][3];
+    for (int a = 0; a < 3; ++a) {
+        geo.n[a] = grid[a];
+        for (int c = 0; c < 3; ++c) {
+            geo.ainv[3 * a + c] = m[a][3 + c];
+            J[a][c] = grid[a] * m[a][3 + c];
+            geo.J[3 * a + c] = (float)J[a][c];
+        }
+    }
+    auto dot = [&](int a, int b) { return J[a][0] * J[b][0] + J[a][1] * J[b][1] + J[a][2] * J[b][2]; };
+    geo.M[0] = (float)dot(0, 0);
+    geo.M[1] = (float)dot(1, 1);
+    geo.M[2] = (float)dot(2, 2);
+    geo.M[3] = (float)dot(0, 1);
+    geo.M[4] = (float)dot(0, 2);
+    geo.M[5] = (float)dot(1, 2);
+    geo.norm = norm == BLIP_NORM_ALFE_GILLAN ? 3.375f : 1.0f;
+    return BLIP_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int size_class(int n_elec)
+{
+    int c = 0;
+    while (n_elec > 1) { n_elec >>= 1; ++c; }
+    return c;
+}
+
+KernelChoice pick(const blip_table_s *t, int n_elec)
+{
+    if (t->auto_mode) {
+        auto it = t->tuned.find(size_class(n_elec));
+        if (it != t->tuned.end()) return it->second;
+    }
+    return t->choice;
+}
+
+int validate_eval(const blip_table_s *t, const double *pos, int n_elec, const int *offs,
+                  int n_walkers, const void *values, const void *grads, const void *laps)
+{
+    if (!t || n_elec < 0) return BLIP_ERR_INVALID_ARG;
+    if (n_elec > 0 && (!pos || !values)) return BLIP_ERR_INVALID_ARG;
+    if ((grads == nullptr) != (laps == nullptr)) return BLIP_ERR_INVALID_ARG;
+    if (offs && n_walkers < 1) return BLIP_ERR_INVALID_ARG;
+    return BLIP_OK;
+}
+
+int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs, int n_walkers,
+                void *values, void *grads, void *laps, cudaStream_t stream, const KernelChoice &kc)
+{
+    if (n_elec == 0) return BLIP_OK;
+    EvalParams p{};
+    p.table = t->d_table;
+    p.scales = t->d_scales;
+    p.row_stride = t->row_stride;
+    p.Lreal = t->Lreal;
+    p.nchunk = t->nchunk;
+    p.groups = (t->nchunk + kc.chunks - 1) / kc.chunks;
+    p.items = (long long)n_elec * p.groups;
+    p.geo = t->geo;
+    p.pos = pos;
+    p.n_elec = n_elec;
+    p.perm = nullptr;
+    p.offsets = offs;
+    p.n_walkers = offs ? n_walkers : 0;
+    p.values = static_cast<float *>(values);
+    p.grads = static_cast<float *>(grads);
+    p.laps = static_cast<float *>(laps);
+    p.vec_out = (t->Lreal % 4 == 0) && aligned16(values) && (!grads || (aligned16(grads) && aligned16(laps)));
+    p.status = t->d_status;
+    CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
+    t->last_stream = stream;
+    t->used = true;
+    return BLIP_OK;
+}
+
+int grow_stage(blip_table_s *t, size_t bytes)
+{
+    if (t->stage_bytes >= bytes) return BLIP_OK;
+    if (t->stage) cudaFree(t->stage);
+    t->stage = nullptr;
+    t->stage_bytes = 0;
+    CK(cudaMalloc(&t->stage, bytes));
+    t->stage_bytes = bytes;
+    return BLIP_OK;
+}
+
+void free_table(blip_table_s *t)
+{
+    if (!t) return;
+    if (!t->d_table && !t->d_scales && !t->d_status && !t->stage && !t->own_stream) {
+        delete t;
+        return;
+    }
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != t->device) cudaSetDevice(t->device);
+    if (t->d_table) cudaFree(t->d_table);
+    if (t->d_scales) cudaFree(t->d_scales);
+    if (t->d_status) cudaFree(t->d_status);
+    if (t->stage) cudaFree(t->stage);
+    if (t->own_stream) cudaStreamDestroy(t->own_stream);
+    if (cur >= 0 && cur != t->device) cudaSetDevice(cur);
+    delete t;
+}
+
+int create_impl(const int grid[3], const double lattice[9], int n_orb, int storage, int norm,
+                const void *coeffs, int coeffs_is_double, int coeffs_on_device, blip_table_s *t)
+{
+    int rc = make_geometry(grid, lattice, norm, t->geo);   // host-only checks first
+    if (rc) return rc;
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return BLIP_ERR_NO_DEVICE;
+    }
+    CK(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3) return BLIP_ERR_NO_DEVICE;   // sm_103 only
+    t->device = dev;
+    t->sm_count = prop.multiProcessorCount;
+    memcpy(t->grid, grid, sizeof(t->grid));
+    t->n_orb = n_orb;
+    t->storage = storage;
+    t->norm = norm;
+    t->is_complex = storage == BLIP_C64 || storage == BLIP_BF16PAIR;
+    t->elem = (storage == BLIP_BF16 || storage == BLIP_BF16PAIR) ? ELEM_BF16
+            : storage == BLIP_F16 ? ELEM_F16 : ELEM_F32;
+    t->Lreal = n_orb * (t->is_complex ? 2 : 1);
+    const int vec = elem_vec(t->elem);
+    t->nchunk = (t->Lreal + 32 * vec - 1) / (32 * vec);
+    t->row_stride = (long long)t->nchunk * 32 * vec;
+    t->rows = (long long)grid[0] * grid[1] * (grid[2] + 3);
+    const long long src_rows = (long long)grid[0] * grid[1] * grid[2];
+    t->choice = KernelChoice{VAR_REGISTER, 1, 8, 0};
+
+    CK(cudaStreamCreateWithFlags(&t->own_stream, cudaStreamNonBlocking));
+    cudaStream_t s = t->own_stream;
+    CK(cudaMalloc(&t->d_status, sizeof(int)));
+    CK(cudaMemsetAsync(t->d_status, 0, sizeof(int), s));
+
+    // 1. FP32 table in the ghost-plane layout
+    const size_t f32_bytes = (size_t)t->rows * t->row_stride * sizeof(float);
+    float *f32 = nullptr;
+    CK(cudaMalloc(&f32, f32_bytes));
+    const size_t esz = coeffs_is_double ? 8 : 4;
+    const size_t src_row_bytes = (size_t)t->Lreal * esz;
+    if (coeffs_on_device) {
+        cudaError_t e = launch_stage_rows(coeffs, coeffs_is_double, 0, src_rows, t->geo,
+                                          t->Lreal, t->row_stride, f32, s);
+        if (e != cudaSuccess) { cudaFree(f32); return cuda_fail(e); }
+    } else {
+        // host source: stream it through a bounded device buffer
+        long long slab = std::max<long long>(1, (64LL << 20) / (long long)src_row_bytes);
+        slab = std::min(slab, src_rows);
+        void *tmp = nullptr;
+        cudaError_t e = cudaMalloc(&tmp, (size_t)slab * src_row_bytes);
+        if (e != cudaSuccess) { cudaFree(f32); return cuda_fail(e); }
+        for (long long r0 = 0; r0 < src_rows && e == cudaSuccess; r0 += slab) {
+            const long long nr = std::min(slab, src_rows - r0);
+            e = cudaMemcpyAsync(tmp, static_cast<const char *>(coeffs) + (size_t)r0 * src_row_bytes,
+                                (size_t)nr * src_row_bytes, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = launch_stage_rows(tmp, coeffs_is_double, r0, nr, t->geo, t->Lreal,
+                                      t->row_stride, f32, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // tmp is reused
+        }
+        cudaFree(tmp);
+        if (e != cudaSuccess) { cudaFree(f32); return cuda_fail(e); }
+    }
+
+    if (t->elem == ELEM_F32) {
+        t->d_table = f32;
+        t->table_bytes = f32_bytes;
+    } else {
+        // 2. per-component scales, then quantise
+        std::vector<float> ones((size_t)t->row_stride, 1.0f);
+        unsigned int *bits = nullptr;
+        cudaError_t e = cudaMalloc(&t->d_scales, sizeof(float) * (size_t)t->row_stride);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(t->d_scales, ones.data(), sizeof(float) * ones.size(),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMalloc(&bits, sizeof(unsigned int) * (size_t)t->Lreal);
+        if (e == cudaSuccess) e = launch_absmax(f32, t->rows, t->row_stride, t->Lreal, bits, s);
+        if (e == cudaSuccess)
+            e = launch_make_scales(bits, t->Lreal, t->is_complex ? 1 : 0, t->d_scales, s);
+        const size_t qbytes = (size_t)t->rows * t->row_stride * 2;
+        if (e == cudaSuccess) e = cudaMalloc(&t->d_table, qbytes);
+        if (e == cudaSuccess)
+            e = launch_quantize(f32, t->rows, t->row_stride, t->Lreal, t->d_scales, t->elem,
+                                t->d_table, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (bits) cudaFree(bits);
+        cudaFree(f32);
+        if (e != cudaSuccess) return cuda_fail(e);
+        t->table_bytes = qbytes;
+    }
+    CK(cudaStreamSynchronize(s));
+    return BLIP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *blip_strerror(int code)
+{
+    switch (code) {
+    case BLIP_OK: return "ok";
+    case BLIP_ERR_INVALID_ARG: return "invalid argument";
+    case BLIP_ERR_SINGULAR_LATTICE: return "singular lattice";
+    case BLIP_ERR_OOM: return "out of memory";
+    case BLIP_ERR_CUDA: return "CUDA error";
+    case BLIP_ERR_UNSUPPORTED_DTYPE: return "unsupported storage kind";
+    case BLIP_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    default: return "unknown error";
+    }
+}
+
+int blip_last_cuda_error(void) { return g_last_cuda_error; }
+
+int blip_create(const int grid[3], const double lattice[9], int n_orb, int storage, int norm,
+                const void *coeffs, int coeffs_is_double, int coeffs_on_device, blip_table *out)
+{
+    if (!out) return BLIP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid || !lattice || !coeffs || n_orb < 1) return BLIP_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (grid[a] < 4 || grid[a] > (1 << 20)) return BLIP_ERR_INVALID_ARG;
+    if ((long long)grid[0] * grid[1] * (grid[2] + 3) >= (1LL << 31)) return BLIP_ERR_INVALID_ARG;
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(lattice[i])) return BLIP_ERR_INVALID_ARG;
+    if (storage < BLIP_F32 || storage > BLIP_BF16PAIR) return BLIP_ERR_UNSUPPORTED_DTYPE;
+    if (norm != BLIP_NORM_BSPLINE && norm != BLIP_NORM_ALFE_GILLAN) return BLIP_ERR_INVALID_ARG;
+    if (n_orb > (1 << 24)) return BLIP_ERR_INVALID_ARG;
+    blip_table_s *t = new (std::nothrow) blip_table_s();
+    if (!t) return BLIP_ERR_OOM;
+    int rc = create_impl(grid, lattice, n_orb, storage, norm, coeffs, coeffs_is_double,
+                         coeffs_on_device, t);
+    if (rc != BLIP_OK) {
+        free_table(t);
+        return rc;
+    }
+    *out = t;
+    return BLIP_OK;
+}
+
+int blip_destroy(blip_table t)
+{
+    if (!t) return BLIP_OK;
+    if (t->used) {
+        cudaStreamSynchronize(t->last_stream);
+    }
+    free_table(t);
+    return BLIP_OK;
+}
+
+int blip_eval(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+              int n_walkers, void *values, void *grads, void *laps, void *stream)
+{
+    int rc = validate_eval(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps);
+    if (rc) return rc;
+    return eval_device(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps,
+                       static_cast<cudaStream_t>(stream), pick(t, n_elec));
+}
+
+int blip_eval_host(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+                   int n_walkers, void *values, void *grads, void *laps)
+{
+    int rc = validate_eval(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps);
+    if (rc) return rc;
+    if (n_elec == 0) return BLIP_OK;
+    const size_t L = (size_t)t->Lreal;
+    const size_t pos_b = (size_t)n_elec * 3 * sizeof(double);
+    const size_t off_b = walker_offsets ? (size_t)(n_walkers + 1) * sizeof(int) : 0;
+    const size_t val_b = (size_t)n_elec * L * sizeof(float);
+    const size_t out_b = grads ? 5 * val_b : val_b;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    rc = grow_stage(t, up(pos_b) + up(off_b) + out_b);
+    if (rc) return rc;
+    char *base = static_cast<char *>(t->stage);
+    double *d_pos = reinterpret_cast<double *>(base);
+    int *d_off = walker_offsets ? reinterpret_cast<int *>(base + up(pos_b)) : nullptr;
+    float *d_val = reinterpret_cast<float *>(base + up(pos_b) + up(off_b));
+    float *d_grd = grads ? d_val + (size_t)n_elec * L : nullptr;
+    float *d_lap = grads ? d_grd + (size_t)n_elec * 3 * L : nullptr;
+    cudaStream_t s = t->own_stream;
+    CK(cudaMemcpyAsync(d_pos, pos, pos_b, cudaMemcpyHostToDevice, s));
+    if (d_off) CK(cudaMemcpyAsync(d_off, walker_offsets, off_b, cudaMemcpyHostToDevice, s));
+    rc = eval_device(t, d_pos, n_elec, d_off, n_walkers, d_val, d_grd, d_lap, s, pick(t, n_elec));
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(values, d_val, val_b, cudaMemcpyDeviceToHost, s));
+    if (grads) {
+        CK(cudaMemcpyAsync(grads, d_grd, 3 * val_b, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(laps, d_lap, val_b, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return BLIP_OK;
+}
+
+int blip_status(blip_table t, int *device_status)
+{
+    if (!t || !device_status) return BLIP_ERR_INVALID_ARG;
+    if (t->used) CK(cudaStreamSynchronize(t->last_stream));
+    int h = 0;
+    CK(cudaMemcpy(&h, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(t->d_status, 0, sizeof(int)));
+    *device_status = h;
+    return BLIP_OK;
+}
+
+int blip_info(blip_table t, long long out[8])
+{
+    if (!t || !out) return BLIP_ERR_INVALID_ARG;
+    out[0] = t->rows;
+    out[1] = t->row_stride;
+    out[2] = t->Lreal;
+    out[3] = elem_bytes(t->elem);
+    out[4] = (long long)t->table_bytes;
+    out[5] = t->storage;
+    out[6] = t->sm_count;
+    out[7] = t->auto_mode ? VAR_AUTO : t->choice.variant;
+    return BLIP_OK;
+}
+
+int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
+{
+    if (!t) return BLIP_ERR_INVALID_ARG;
+    if (variant == VAR_AUTO) {
+        t->auto_mode = true;
+        return BLIP_OK;
+    }
+    if (variant != VAR_REGISTER) return BLIP_ERR_INVALID_ARG;
+    const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
+    if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
+    if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
+    if (sort != 0) return BLIP_ERR_INVALID_ARG;
+    t->auto_mode = false;
+    t->choice = KernelChoice{variant, chunks, warps, sort};
+    return BLIP_OK;
+}
+
+int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+                  int n_walkers, void *values, void *grads, void *laps, void *stream,
+                  int chosen[4])
+{
+    int rc = validate_eval(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps);
+    if (rc) return rc;
+    if (n_elec == 0) return BLIP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<KernelChoice> cands;
+    const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
+    for (int c = 1; c <= max_chunks; ++c)
+        for (int w : {4, 8, 16}) cands.push_back(KernelChoice{VAR_REGISTER, c, w, 0});
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    KernelChoice bestc = cands[0];
+    for (const KernelChoice &kc : cands) {
+        rc = eval_device(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps, s, kc);
+        if (rc) break;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3 && rc == 0; ++rep) {
+            cudaEventRecord(e0, s);
+            rc = eval_device(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps, s, kc);
+            cudaEventRecord(e1, s);
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) { rc = cuda_fail(ce); break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tmin = std::min(tmin, ms);
+        }
+        if (rc) break;
+        if (tmin < best) { best = tmin; bestc = kc; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    t->tuned[size_class(n_elec)] = bestc;
+    t->auto_mode = true;
+    if (chosen) {
+        chosen[0] = bestc.variant;
+        chosen[1] = bestc.chunks;
+        chosen[2] = bestc.warps;
+        chosen[3] = bestc.sort;
+    }
+    return BLIP_OK;
+}
+
+int blip_graph_create(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+                      int n_walkers, void *values, void *grads, void *laps, int per_launch,
+                      blip_graph *out)
+{
+    if (!out) return BLIP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate_eval(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps);
+    if (rc) return rc;
+    if (n_elec < 1 || per_launch < 1) return BLIP_ERR_INVALID_ARG;
+    blip_graph_s *g = new (std::nothrow) blip_graph_s();
+    if (!g) return BLIP_ERR_OOM;
+    g->table = t;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e); }
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    const size_t L = (size_t)t->Lreal;
+    for (int e0 = 0; e0 < n_elec && e == cudaSuccess && rc == 0; e0 += per_launch) {
+        const int ne = std::min(per_launch, n_elec - e0);
+        const bool whole = (e0 == 0 && ne == n_elec);
+        rc = eval_device(t, pos + 3 * (size_t)e0, ne, whole ? walker_offsets : nullptr, n_walkers,
+                         static_cast<float *>(values) + (size_t)e0 * L,
+                         grads ? static_cast<float *>(grads) + (size_t)e0 * 3 * L : nullptr,
+                         laps ? static_cast<float *>(laps) + (size_t)e0 * L : nullptr, s,
+                         pick(t, ne));
+    }
+    cudaError_t ee = cudaStreamEndCapture(s, &g->graph);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess && rc == 0) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    cudaStreamDestroy(s);
+    t->last_stream = nullptr;
+    if (e != cudaSuccess || rc != 0) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc ? rc : cuda_fail(e);
+    }
+    *out = g;
+    return BLIP_OK;
+}
+
+int blip_graph_launch(blip_graph g, void *stream)
+{
+    if (!g || !g->exec) return BLIP_ERR_INVALID_ARG;
+    CK(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+    g->table->last_stream = static_cast<cudaStream_t>(stream);
+    g->table->used = true;
+    return BLIP_OK;
+}
+
+int blip_graph_destroy(blip_graph g)
+{
+    if (!g) return BLIP_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return BLIP_OK;
+}
+
+}  // extern "C"

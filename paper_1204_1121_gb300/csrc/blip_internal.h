@@ -1,0 +1,78 @@
+// Internal declarations shared by the CUDA translation units of libblip.
+// Not part of the public ABI (include/blip.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace blip {
+
+// Element kinds of the stored table.
+enum Elem { ELEM_F32 = 0, ELEM_BF16 = 1, ELEM_F16 = 2 };
+
+// Kernel variants.
+enum Variant { VAR_AUTO = 0, VAR_REGISTER = 1, VAR_BULK = 2 };
+
+// Cell geometry, prepared once on the host in FP64.
+struct Geometry {
+    int n[3];          // grid points along a_1, a_2, a_3
+    double ainv[9];    // A^{-1}, row-major: u_a = sum_c ainv[3a + c] r_c
+    float J[9];        // J = diag(n) A^{-1}, row-major J[3a + c]
+    float M[6];        // J J^T entries xx, yy, zz, xy, xz, yz
+    float norm;        // 1, or (3/2)^3 for phi(0) = 1 blips
+};
+
+// Everything one evaluation launch needs (passed by value as the kernel
+// parameter).
+struct EvalParams {
+    const void *table;      // rows [n1][n2][n3 + 3][row_stride] of the stored element
+    const float *scales;    // [Lreal] per-component scale, or nullptr
+    long long row_stride;   // stored elements per row (padded)
+    int Lreal;              // real components per row (n_orb, or 2 n_orb if complex)
+    int nchunk;             // 16-byte-per-lane chunks per row: ceil(Lreal / (32 * VEC))
+    int groups;             // chunk groups per electron: ceil(nchunk / chunks per warp)
+    long long items;        // n_elec * groups
+    Geometry geo;
+    const double *pos;      // [n_elec][3]
+    int n_elec;
+    const int *perm;        // evaluation order of the electrons, or nullptr
+    const int *offsets;     // [n_walkers + 1] or nullptr
+    int n_walkers;
+    float *values;          // [n_elec][Lreal]
+    float *grads;           // [n_elec][3][Lreal] or nullptr (values only)
+    float *laps;            // [n_elec][Lreal] or nullptr
+    int vec_out;            // 1: outputs may be written with 16-byte stores
+    int *status;            // device status word (atomicOr)
+};
+
+// Stored elements per 16-byte vector.
+inline int elem_vec(int elem) { return elem == ELEM_F32 ? 4 : 8; }
+inline int elem_bytes(int elem) { return elem == ELEM_F32 ? 4 : 2; }
+
+// Launch the evaluation kernel.  chunks in {1, 2, 3}; warps in [1, 16].
+cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, int warps,
+                        cudaStream_t stream);
+
+// Optional spatial sort: writes perm[n_elec] (electron ids ordered by grid
+// brick).  scratch must hold sort_scratch_bytes(n_elec) bytes.
+size_t sort_scratch_bytes(int n_elec, const Geometry &geo);
+cudaError_t launch_sort(const Geometry &geo, const double *pos, int n_elec, void *scratch,
+                        int **perm_out, cudaStream_t stream);
+
+// Table construction kernels (blip_table.cu).
+// Convert rows [row0, row0 + nrows) of a source table [n1*n2*n3][Lreal]
+// (src points at row row0) into the FP32 ghost-plane layout.
+cudaError_t launch_stage_rows(const void *src, int src_is_double, long long row0, long long nrows,
+                              const Geometry &geo, int Lreal, long long row_stride, float *dst,
+                              cudaStream_t stream);
+// Per-component max |a| over the stored FP32 table (ghost rows included).
+cudaError_t launch_absmax(const float *table, long long rows, long long row_stride, int Lreal,
+                          unsigned int *absmax_bits, cudaStream_t stream);
+// scales[l] from the max |a| bits (pairs = 1: complex pairs share one scale).
+cudaError_t launch_make_scales(const unsigned int *absmax_bits, int Lreal, int pairs,
+                               float *scales, cudaStream_t stream);
+// Quantise the FP32 table into BF16 / FP16 with the per-component scales.
+cudaError_t launch_quantize(const float *src, long long rows, long long row_stride, int Lreal,
+                            const float *scales, int elem, void *dst, cudaStream_t stream);
+
+}  // namespace blip

@@ -1,0 +1,322 @@
+"""CUDA path (through the C ABI) against the FP64 oracle.
+
+Every comparison is element by element under the bound documented in
+``gpu_util`` (FP32: 8e-6 x sum_s |W||a|; quantised tables add the storage
+unit roundoff).  Small cases compare every output; the full-size TiO2-shaped
+workloads compare a seeded sample of electrons in the launch configuration the
+benchmark uses.
+"""
+import numpy as np
+import pytest
+
+import blip_inputs as bi
+import oracle
+import pins
+from gpu_util import TAU32, cached_table, compare, gpu_eval
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1204_1121_gb300 as pb
+    return pb
+
+
+def _edge_positions(lat, grid, rng, n=96):
+    n_ = np.array(grid, dtype=np.float64)
+    u = [rng.uniform(-2.0, 3.0, size=(n, 3)),
+         rng.uniform(0, 1, size=(8, 3)) + rng.integers(-50, 50, size=(8, 3)),
+         (rng.integers(0, 64, size=(8, 3)) % n_) / n_,           # exact nodes
+         np.full((1, 3), 1.0 - 2.0 ** -53), np.full((1, 3), -2.0 ** -60),
+         np.array([[0.0, 0.5, 1.0], [1e6, -1e6, 3e5]])]
+    return np.concatenate(u) @ lat
+
+
+def _scales(tab, pairs):
+    a = np.abs(tab.reshape(-1, tab.shape[-1] if not np.iscomplexobj(tab) else tab.shape[-1]))
+    if np.iscomplexobj(tab):
+        r = np.abs(tab.view(np.float64).reshape(-1, 2 * tab.shape[-1])).max(0)
+        r = np.maximum(r[0::2], r[1::2]).repeat(2)
+        return np.where(r > 0, r, 1.0)
+    s = a.max(0)
+    return np.where(s > 0, s, 1.0)
+
+
+# ---------------------------------------------------------------------------
+# small cases: every output
+# ---------------------------------------------------------------------------
+
+def test_cubic16_fp32_all_outputs(pb):
+    w, tab = cached_table("cubic16")
+    pos, _ = w.positions()
+    t = pb.BlipTable(w.grid, w.lattice, tab, storage=pb.F32)
+    out = gpu_eval(t, pos)
+    st = compare(w.grid, w.lattice, tab, pos, out)
+    assert st["value"]["max_bound_ratio"] <= 1.0
+    assert t.status() == 0
+
+
+@pytest.mark.parametrize("L", [1, 5, 37, 128, 300, 769])
+def test_triclinic_ragged_orbitals_and_edge_positions(pb, L):
+    rng = np.random.default_rng(L)
+    grid = (9, 7, 11)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, L, seed=L, sigma=2.0)
+    pos = _edge_positions(lat, grid, rng)
+    t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
+    compare(grid, lat, tab, pos, gpu_eval(t, pos))
+
+
+@pytest.mark.parametrize("grid", [(4, 4, 4), (5, 4, 7), (4, 9, 4)])
+def test_tiny_grids_against_bruteforce(pb, grid):
+    rng = np.random.default_rng(sum(grid))
+    lat = pins.triclinic_lattice()
+    tab = rng.normal(size=grid + (6,))
+    pos = _edge_positions(lat, grid, rng, n=24)
+    t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
+    v, g, lp = gpu_eval(t, pos)
+    vb, gb, lb = oracle.brute.eval_brute(grid, lat, tab, pos)
+    _, _, _, mag = oracle.eval_stencil(grid, lat, tab, pos, absmag=True)
+    assert (np.abs(v - vb) <= TAU32 * mag[:, 0] + 1e-12).all()
+    assert (np.abs(g - gb) <= TAU32 * mag[:, 1:4] + 1e-11).all()
+    assert (np.abs(lp - lb) <= TAU32 * mag[:, 4] + 1e-10).all()
+
+
+def test_kernel_configs_bitwise_identical(pb):
+    w, tab = cached_table("cubic16")
+    rng = np.random.default_rng(11)
+    grid = (8, 9, 10)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 700, seed=5)
+    pos = _edge_positions(lat, grid, rng)
+    t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
+    ref = gpu_eval(t, pos)
+    for chunks in (1, 2, 3):
+        for warps in (1, 4, 16):
+            t.set_kernel(1, chunks, warps, 0)
+            out = gpu_eval(t, pos)
+            for a, b in zip(ref, out):
+                assert np.array_equal(a, b), (chunks, warps)
+
+
+def test_values_only_matches_full(pb):
+    grid = (8, 8, 8)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 260, seed=2)
+    pos = _edge_positions(lat, grid, np.random.default_rng(2))
+    t = pb.BlipTable(grid, lat, tab)
+    full = gpu_eval(t, pos)
+    vo = gpu_eval(t, pos, values_only=True)
+    assert np.array_equal(full[0], vo[0])
+
+
+def test_alfe_gillan_normalisation(pb):
+    grid = (6, 6, 6)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 16, seed=4)
+    pos = _edge_positions(lat, grid, np.random.default_rng(4))
+    t = pb.BlipTable(grid, lat, tab, norm=pb.NORM_ALFE_GILLAN)
+    compare(grid, lat, tab, pos, gpu_eval(t, pos), norm=1)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_quantised_storage_bound(pb, storage):
+    grid = (10, 9, 8)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 100, seed=7)
+    pos = _edge_positions(lat, grid, np.random.default_rng(7))
+    kind = pb.BF16 if storage == "bf16" else pb.F16
+    t = pb.BlipTable(grid, lat, tab, storage=kind)
+    st = compare(grid, lat, tab, pos, gpu_eval(t, pos), storage=kind, scales=_scales(tab, False))
+    # the rounding is really there: the error is well above the FP32 path's
+    assert st["value"]["max_rel_to_C"] > 10 * 2.0 ** -24
+
+
+@pytest.mark.parametrize("storage", ["c64", "bf16pair"])
+def test_complex_storage(pb, storage):
+    grid = (8, 10, 6)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 70, seed=8, is_complex=True)
+    pos = _edge_positions(lat, grid, np.random.default_rng(8))
+    kind = pb.C64 if storage == "c64" else pb.BF16PAIR
+    t = pb.BlipTable(grid, lat, tab, storage=kind)
+    out = gpu_eval(t, pos)
+    compare(grid, lat, tab, pos, out, storage=kind, scales=_scales(tab, True))
+    v = pb.BlipTable.as_complex(out[0])
+    assert v.shape == (len(pos), 70) and v.dtype == np.complex64
+
+
+def test_plane_wave_table_on_gpu(pb):
+    """A closed-form table: the GPU reproduces exp(i theta.g) at nodes."""
+    grid = (12, 10, 8)
+    lat = pins.triclinic_lattice()
+    tab, th, D = pins.plane_wave_table(grid, (2, -3, 1), True)
+    n = np.array(grid, dtype=np.float64)
+    rng = np.random.default_rng(9)
+    mm = np.stack([rng.integers(0, k, 40) for k in grid], 1).astype(np.float64)
+    pos = ((mm + n * rng.integers(-3, 4, size=(40, 3))) / n) @ lat
+    t = pb.BlipTable(grid, lat, tab, storage=pb.C64)
+    v = pb.BlipTable.as_complex(gpu_eval(t, pos)[0])[:, 0]
+    assert np.abs(v - np.exp(1j * (mm @ th))).max() < 2e-5
+
+
+def test_nonfinite_and_far_positions_flagged(pb):
+    grid = (6, 6, 6)
+    lat = np.diag([6.0, 6.0, 6.0])
+    tab = bi.smooth_random_table(grid, 10, seed=1)
+    pos = np.array([[0.5, 0.5, 0.5], [np.nan, 0, 0], [1.0, np.inf, 2.0], [1e13, 0, 0]])
+    t = pb.BlipTable(grid, lat, tab)
+    v, g, lp = gpu_eval(t, pos)
+    assert np.isnan(v[1]).all() and np.isnan(g[2]).all() and np.isnan(lp[1]).all()
+    assert np.isfinite(v[0]).all() and np.isfinite(v[3]).all()
+    st = t.status()
+    assert st & pb.STATUS_NONFINITE_POS and st & pb.STATUS_FAR_POS
+    assert t.status() == 0          # cleared by the read
+
+
+def test_walker_offsets_checked(pb):
+    grid = (5, 5, 5)
+    lat = np.diag([5.0, 5.0, 5.0])
+    tab = bi.smooth_random_table(grid, 4, seed=1)
+    pos = np.random.default_rng(1).uniform(0, 5, size=(10, 3))
+    t = pb.BlipTable(grid, lat, tab)
+    gpu_eval(t, pos, offsets=[0, 3, 3, 10])
+    assert t.status() == 0
+    gpu_eval(t, pos, offsets=[0, 4, 2, 10])
+    assert t.status() & pb.STATUS_BAD_OFFSETS
+    gpu_eval(t, pos, offsets=[0, 4, 9])
+    assert t.status() & pb.STATUS_BAD_OFFSETS
+
+
+def test_empty_batch_and_bad_arguments(pb):
+    grid = (4, 4, 4)
+    t = pb.BlipTable(grid, np.eye(3) * 4, np.ones(grid + (3,)))
+    e = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    v, g, lp = t.eval(e)
+    assert v.shape == (0, 3)
+    L = pb.lib()
+    import ctypes
+    assert L.blip_eval(t.handle, None, 5, None, 0, None, None, None, None) == -1
+    assert L.blip_set_kernel(t.handle, 1, 4, 8, 0) == -1
+    assert L.blip_set_kernel(t.handle, 1, 1, 0, 0) == -1
+    with pytest.raises(pb.BlipError):
+        pb.BlipTable((3, 4, 4), np.eye(3), np.ones((3, 4, 4, 1)))
+
+
+def test_host_entry_point_and_graph_match_device(pb):
+    grid = (8, 8, 8)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 64, seed=3)
+    pos = _edge_positions(lat, grid, np.random.default_rng(3))
+    t = pb.BlipTable(grid, lat, tab)
+    ref = gpu_eval(t, pos)
+    hv, hg, hl = t.eval_host(pos)
+    for a, b in zip(ref, (hv, hg, hl)):
+        assert np.array_equal(a, b)
+    dpos = torch.from_numpy(pos).cuda()
+    for per in (1, 7, len(pos)):
+        out = t.alloc_outputs(len(pos))
+        gr = t.graph(dpos, out, per)
+        gr.launch()
+        torch.cuda.synchronize()
+        for a, b in zip(ref, out):
+            assert np.array_equal(a, b.cpu().numpy()), per
+        gr.close()
+
+
+def test_autotune_keeps_results(pb):
+    grid = (8, 8, 8)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 256, seed=6)
+    pos = _edge_positions(lat, grid, np.random.default_rng(6))
+    t = pb.BlipTable(grid, lat, tab)
+    ref = gpu_eval(t, pos)
+    dpos = torch.from_numpy(pos).cuda()
+    ch = t.autotune(dpos)
+    assert ch[0] in (1, 2) and ch[1] in (1, 2, 3)
+    out = gpu_eval(t, pos)
+    for a, b in zip(ref, out):
+        assert np.array_equal(a, b)
+
+
+def test_repeat_runs_bitwise_identical(pb):
+    w, tab = cached_table("cubic16")
+    pos, _ = w.positions()
+    t = pb.BlipTable(w.grid, w.lattice, tab)
+    a = gpu_eval(t, pos)
+    b = gpu_eval(t, pos)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+# ---------------------------------------------------------------------------
+# full-size TiO2-shaped workloads (sampled electrons)
+# ---------------------------------------------------------------------------
+
+def _sample(n, k, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, size=k)]))
+
+
+def test_tio2_all_at_once_and_one_at_a_time(pb):
+    w, tab = cached_table("tio2")
+    pos, offs = w.positions()
+    t = pb.BlipTable(w.grid, w.lattice, tab, storage=pb.F32)
+    out = gpu_eval(t, pos, offsets=offs)
+    compare(w.grid, w.lattice, tab, pos, out, sample=_sample(len(pos), 96, 1))
+    assert t.status() == 0
+    # one electron per launch (particle-by-particle order), captured in a graph
+    dpos = torch.from_numpy(pos).cuda()
+    o1 = t.alloc_outputs(len(pos))
+    gr = t.graph(dpos, o1, 1)
+    gr.launch()
+    torch.cuda.synchronize()
+    for a, b in zip(out, o1):
+        assert np.array_equal(a, b.cpu().numpy())
+
+
+@pytest.mark.parametrize("batch", [1, 32, 1536])
+def test_tio2_batched_walkers(pb, batch):
+    w, tab = cached_table("tio2")
+    wb = bi.workload("tio2_batch", batch=batch)
+    pos, offs = wb.positions()
+    t = pb.BlipTable(wb.grid, wb.lattice, tab, storage=pb.F32)
+    dpos = torch.from_numpy(pos).cuda()
+    doffs = torch.from_numpy(offs).cuda()
+    t.autotune(dpos, doffs)
+    v, g, lp = t.eval(dpos, doffs)
+    torch.cuda.synchronize()
+    idx = _sample(len(pos), 64, batch)
+    sub = [v[idx].cpu().numpy(), g[idx].cpu().numpy(), lp[idx].cpu().numpy()]
+    compare(wb.grid, wb.lattice, tab, pos[idx], sub)
+    assert t.status() == 0
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_tio2_precision_storage_and_kinetic_energy(pb, storage):
+    """Precision workload shape (1,536 electrons per walker, 768 orbitals):
+    bound check on sampled electrons, and the Slater-only local kinetic
+    energy error per primitive cell (64 cells) below 1e-3 hartree."""
+    w, tab = cached_table("tio2")
+    wp = bi.workload("tio2_precision", n_walkers=4)
+    pos, offs = wp.positions()
+    kind = pb.BF16 if storage == "bf16" else pb.F16
+    t = pb.BlipTable(wp.grid, wp.lattice, tab, storage=kind)
+    out = gpu_eval(t, pos, offsets=offs)
+    compare(wp.grid, wp.lattice, tab, pos, out, storage=kind, scales=_scales(tab, False),
+            sample=_sample(len(pos), 48, 3))
+    # kinetic energy of walker 0: spin up electrons 0..767, spin down 768..1535
+    p0 = pos[:1536]
+    rv, _, rl = oracle.eval_stencil(wp.grid, wp.lattice, tab, p0)
+    blocks = [(0, 768), (768, 1536)]
+    T_ref, conds = oracle.kinetic.local_kinetic(rv, rl, blocks)
+    T_gpu, _ = oracle.kinetic.local_kinetic(out[0][:1536].astype(np.float64),
+                                            out[2][:1536].astype(np.float64), blocks)
+    per_cell = abs(T_gpu - T_ref) / 64.0
+    print(f"\n{storage}: T_L ref {T_ref:.6f} gpu {T_gpu:.6f} |dT|/cell {per_cell:.3e} "
+          f"cond {max(conds):.3e}")
+    assert np.isfinite(T_gpu)
