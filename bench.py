@@ -5,8 +5,8 @@ Laplacian) of the periodic cubic-blip path on GB300.
 Default workload: the TiO2-shaped table (tetragonal 17.4 x 17.4 x 11.2 bohr,
 72 x 72 x 48 grid, 768 real orbitals, FP32 storage) evaluated at 1,536
 uniform positions all at once (one batched launch per step).  A step is one
-blip_eval of the batch; L2 is flushed (512 MB write) between steps outside
-the per-step CUDA-event window.
+blip_eval of the batch; L2 is flushed (512 MB write, then 512 MB read so no
+dirty lines remain) between steps outside the per-step CUDA-event window.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores on the same workload instead.
@@ -78,7 +78,7 @@ def describe(w, args, E):
                      f"{'complex' if w.is_complex else 'real'} orbitals, {E} positions per step"
                      + (f" ({w.n_walkers} walkers)" if w.n_walkers > 1 else " (all at once)"),
          "electrons": E, "orbitals": w.n_orb, "storage": args.storage,
-         "l2": "flushed between steps (512 MB write, outside the event window)",
+         "l2": "flushed between steps (512 MB write + 512 MB read, outside the event window)",
          "positions": "uniform in cell" if w.uniform_n else "walker configs + N(0,0.3^2) moves"}
     return d
 
@@ -105,7 +105,7 @@ def touched_sites(grid, lattice, pos):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("blip_eval.cu", "blip_internal.h"):
+    for f in ("blip_eval.cu", "blip_bulk.cu", "blip_device.cuh", "blip_internal.h"):
         with open(os.path.join(ROOT, "paper_1204_1121_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -267,13 +267,20 @@ def main():
         v_, c_, w_, s_ = (int(x) for x in args.kernel.split(","))
         t.set_kernel(v_, c_, w_, s_)
         chosen = (v_, c_, w_, s_)
+    # L2 flush between steps: write 512 MB, then read another 512 MB so the
+    # L2 is left holding clean lines (no write-back charged to the next step)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_rd = torch.ones(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2(k):
+        flush.fill_(float(k))
+        return flush_rd.sum()
 
     def step():
         t.eval(dpos, doffs, out=out)
 
     for k in range(max(3, args.warmup)):
-        flush.fill_(float(k))
+        flush_l2(k)
         step()
     torch.cuda.synchronize()
     st = t.status()
@@ -289,7 +296,7 @@ def main():
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     for k in range(K):
-        flush.fill_(float(k))
+        flush_l2(k)
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
@@ -328,7 +335,8 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": describe(w, args, E), "roofline": roof, "clocks": clocks,
-            "gpu_launches": K, "kernel_choice": list(chosen), "status": st,
+            "gpu_launches": K * (6 if chosen[3] else 1), "kernel_choice": list(chosen),
+            "status": st,
             "wall_s_timed_region": wall}
 
     if not args.no_e2e:

@@ -49,6 +49,9 @@ struct blip_table_s {
     cudaStream_t own_stream = nullptr;
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    // spatial-sort scratch (grown outside stream capture)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
 };
 
 struct blip_graph_s {
@@ -168,6 +171,25 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
     p.pos = pos;
     p.n_elec = n_elec;
     p.perm = nullptr;
+    if (kc.sort) {
+        const size_t need = sort_scratch_bytes(n_elec, t->geo);
+        if (t->scratch_bytes < need) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            CK(cudaStreamIsCapturing(stream, &cs));
+            if (cs != cudaStreamCaptureStatusNone) return BLIP_ERR_INVALID_ARG;  // no growth in capture
+            if (t->scratch) {
+                CK(cudaStreamSynchronize(t->last_stream));
+                cudaFree(t->scratch);
+            }
+            t->scratch = nullptr;
+            t->scratch_bytes = 0;
+            CK(cudaMalloc(&t->scratch, need));
+            t->scratch_bytes = need;
+        }
+        int *perm = nullptr;
+        CK(launch_sort(t->geo, pos, n_elec, t->scratch, &perm, stream));
+        p.perm = perm;
+    }
     p.offsets = offs;
     p.n_walkers = offs ? n_walkers : 0;
     p.values = static_cast<float *>(values);
@@ -175,7 +197,14 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
     p.laps = static_cast<float *>(laps);
     p.vec_out = (t->Lreal % 4 == 0) && aligned16(values) && (!grads || (aligned16(grads) && aligned16(laps)));
     p.status = t->d_status;
-    CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
+    if (kc.variant == VAR_BULK) {
+        const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
+        int per_sm = (int)((228 * 1024) / (smem + 1024));
+        per_sm = std::max(1, std::min(per_sm, 4));
+        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, stream));
+    } else {
+        CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
+    }
     t->last_stream = stream;
     t->used = true;
     return BLIP_OK;
@@ -195,7 +224,8 @@ int grow_stage(blip_table_s *t, size_t bytes)
 void free_table(blip_table_s *t)
 {
     if (!t) return;
-    if (!t->d_table && !t->d_scales && !t->d_status && !t->stage && !t->own_stream) {
+    if (!t->d_table && !t->d_scales && !t->d_status && !t->stage && !t->scratch &&
+        !t->own_stream) {
         delete t;
         return;
     }
@@ -206,6 +236,7 @@ void free_table(blip_table_s *t)
     if (t->d_scales) cudaFree(t->d_scales);
     if (t->d_status) cudaFree(t->d_status);
     if (t->stage) cudaFree(t->stage);
+    if (t->scratch) cudaFree(t->scratch);
     if (t->own_stream) cudaStreamDestroy(t->own_stream);
     if (cur >= 0 && cur != t->device) cudaSetDevice(cur);
     delete t;
@@ -438,11 +469,18 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         t->auto_mode = true;
         return BLIP_OK;
     }
-    if (variant != VAR_REGISTER) return BLIP_ERR_INVALID_ARG;
-    const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
-    if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
-    if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
-    if (sort != 0) return BLIP_ERR_INVALID_ARG;
+    if (variant == VAR_REGISTER) {
+        const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
+        if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
+        if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
+    } else if (variant == VAR_BULK) {
+        // chunks = consumer warps per CTA (chunks per tile), warps = pipeline stages
+        if (chunks < 1 || chunks > 8 || warps < 2 || warps > 32) return BLIP_ERR_INVALID_ARG;
+        if (bulk_smem_bytes(chunks, warps) > 227 * 1024) return BLIP_ERR_INVALID_ARG;
+    } else {
+        return BLIP_ERR_INVALID_ARG;
+    }
+    if (sort != 0 && sort != 1) return BLIP_ERR_INVALID_ARG;
     t->auto_mode = false;
     t->choice = KernelChoice{variant, chunks, warps, sort};
     return BLIP_OK;
@@ -458,8 +496,19 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<KernelChoice> cands;
     const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
-    for (int c = 1; c <= max_chunks; ++c)
-        for (int w : {4, 8, 16}) cands.push_back(KernelChoice{VAR_REGISTER, c, w, 0});
+    std::vector<int> tws;
+    for (int d : {1, 2, 3, 4, 6})
+        tws.push_back(std::min(8, (t->nchunk + d - 1) / d));
+    std::sort(tws.begin(), tws.end());
+    tws.erase(std::unique(tws.begin(), tws.end()), tws.end());
+    for (int srt = 0; srt <= (n_elec >= 4096 ? 1 : 0); ++srt) {
+        for (int c = 1; c <= max_chunks; ++c)
+            for (int w : {4, 8, 16}) cands.push_back(KernelChoice{VAR_REGISTER, c, w, srt});
+        for (int tw : tws)
+            for (int st : {4, 8, 16})
+                if (bulk_smem_bytes(tw, st) <= 227 * 1024)
+                    cands.push_back(KernelChoice{VAR_BULK, tw, st, srt});
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

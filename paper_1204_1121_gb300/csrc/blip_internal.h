@@ -49,9 +49,16 @@ struct EvalParams {
 inline int elem_vec(int elem) { return elem == ELEM_F32 ? 4 : 8; }
 inline int elem_bytes(int elem) { return elem == ELEM_F32 ? 4 : 2; }
 
-// Launch the evaluation kernel.  chunks in {1, 2, 3}; warps in [1, 16].
+// Launch the register-gather kernel.  chunks in {1, 2, 3} (1 for 16-bit
+// elements); warps in [1, 16].
 cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, int warps,
                         cudaStream_t stream);
+
+// Launch the bulk-copy kernel: tw chunks per tile (consumer warps, 1..8),
+// `stages` shared-memory stages, ctas_per_sm persistent CTAs per SM.
+cudaError_t launch_bulk(const EvalParams &p, int elem, int tw, int stages, int ctas_per_sm,
+                        int sm_count, cudaStream_t stream);
+size_t bulk_smem_bytes(int tw, int stages);
 
 // Optional spatial sort: writes perm[n_elec] (electron ids ordered by grid
 // brick).  scratch must hold sort_scratch_bytes(n_elec) bytes.

@@ -89,3 +89,21 @@ def compare(grid, lattice, coeffs, pos, gpu_out, storage=0, norm=0, scales=None,
         assert not bad.any(), (f"{name}: {int(bad.sum())} outputs break the bound; "
                                f"worst ratio {float(np.nanmax(ratio)):.3g}")
     return stats
+
+
+def kinetic_error_bound(values, laps, bound_v, bound_l, blocks):
+    """First-order bound on |T_L(gpu) - T_L(ref)| from elementwise output
+    bounds.  With X = D^{-1} Lap,
+        dT = -1/2 [tr(D^{-1} dLap) - tr(D^{-1} dD X)],
+    so |dT| <= 1/2 [sum |D^{-1}|^T * B_lap + sum |X D^{-1}|^T * B_val]
+    (elementwise products summed), per spin block."""
+    total = 0.0
+    for j0, j1 in blocks:
+        m = j1 - j0
+        D = np.asarray(values[j0:j1, :m], dtype=np.float64)
+        Lp = np.asarray(laps[j0:j1, :m], dtype=np.float64)
+        Di = np.linalg.inv(D)
+        X = Di @ Lp
+        total += 0.5 * (np.sum(np.abs(Di).T * bound_l[j0:j1, :m])
+                        + np.sum(np.abs(X @ Di).T * bound_v[j0:j1, :m]))
+    return total
