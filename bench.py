@@ -68,7 +68,8 @@ def make_workload(args, rank):
     if args.walkers:
         kw["n_walkers"] = args.walkers
     w = bi.workload(args.workload, **kw)
-    w.pos_seed += 1000 * rank          # each rank evaluates its own walkers
+    from paper_1204_1121_gb300 import replicas
+    w.pos_seed = replicas.weak_seed(w.pos_seed, rank)   # each rank: its own walkers
     return w
 
 
@@ -241,6 +242,7 @@ def main():
         return run_reference(args)
     import torch
     import paper_1204_1121_gb300 as pb
+    from paper_1204_1121_gb300 import replicas
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -306,11 +308,7 @@ def main():
     wall = time.perf_counter() - w0
     clocks = sampler.stop()
     per = [a.elapsed_time(b) for a, b in evs]
-    ms = statistics.mean(per)
-    if dist:
-        x = torch.tensor([ms], device="cuda")
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms = float(x.item())
+    ms = replicas.max_over_ranks(statistics.mean(per))
     evals = E * w.n_orb
     value = world * evals / (ms / 1e3)
 
@@ -354,11 +352,7 @@ def main():
             t0 = time.perf_counter()
             t.eval_host(hp, ho, out=(hv, hg, hl))
             tt.append(time.perf_counter() - t0)
-        e_ms = 1e3 * statistics.mean(tt)
-        if dist:
-            x = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(x, op=dist.ReduceOp.MAX)
-            e_ms = float(x.item())
+        e_ms = replicas.max_over_ranks(1e3 * statistics.mean(tt))
         line["e2e"] = {"value": world * evals / (e_ms / 1e3), "unit": "orbital*electron evals/s",
                        "h2d_bytes_per_step": int(hp.numel() * 8 + ho.numel() * 4),
                        "d2h_bytes_per_step": int((hv.numel() + hg.numel() + hl.numel()) * 4),
