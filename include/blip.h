@@ -53,6 +53,7 @@ extern "C" {
 #define BLIP_ERR_CUDA              -4  /* a CUDA call failed (see blip_last_cuda_error) */
 #define BLIP_ERR_UNSUPPORTED_DTYPE -5  /* storage kind not known                 */
 #define BLIP_ERR_NO_DEVICE         -6  /* no CUDA device, or not an sm_103 part  */
+#define BLIP_ERR_SCRATCH_LIMIT     -7  /* batch too large for the fixed no-allocation scratch */
 
 /* ---- device-side status bits (reported by blip_status) ---------------- */
 #define BLIP_STATUS_NONFINITE_POS  0x1 /* a position was NaN/Inf: its outputs are NaN    */
@@ -200,6 +201,42 @@ int blip_graph_create(blip_table t, const double *pos, int n_elec, const int *wa
                       blip_graph *out);
 int blip_graph_launch(blip_graph g, void *stream);
 int blip_graph_destroy(blip_graph g);
+
+/*
+ * blip_eval_sorted_noalloc - blip_eval with the electrons sorted by grid cell,
+ * for callers that must not allocate device memory during an evaluation.
+ *
+ * No counterpart in the paper: this is a service of the library.  Some
+ * callers cannot let a library call cudaMalloc: code that is being recorded
+ * into a CUDA graph (an allocation is not allowed in the middle of a stream
+ * capture), and Monte Carlo drivers or frameworks that hand all device memory
+ * to their own pool at start-up and run with a fixed budget (there a new
+ * allocation can fail, fragment the pool, or synchronise the device in the
+ * middle of a step).  blip_eval with the sort enabled grows its scratch with
+ * cudaMalloc the first time a batch needs more; this entry point instead
+ * takes the sort's scratch (histogram, keys, permutation) from one fixed
+ * 8 MiB device buffer built into the library, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Arguments, layouts, results and errors are those of blip_eval; the
+ * evaluation kernel is the table's current choice (blip_set_kernel /
+ * blip_autotune), always run on the cell-sorted order.
+ * Limit: the scratch needed is about 4 (n1 n2 n3 + 1) + 8 n_elec bytes; a
+ * batch that needs more than 8 MiB returns BLIP_ERR_SCRATCH_LIMIT and does
+ * nothing (about 0.9 million electrons on the 72 x 72 x 48 grid).
+ * The table's device must be the current device.  The first call on a device
+ * looks up the buffer's device address (which may load the library's code on
+ * that device); make that first call before any stream capture.
+ * Every device that loads the library holds the 8 MiB buffer until the
+ * process exits.  All calls on a device share the one buffer and it keeps the
+ * last call's contents (the call clears what must start at zero itself), so
+ * calls whose work can overlap on the GPU - on different streams without an
+ * ordering between them, or from several threads - race on it and give wrong
+ * results; order them on one stream.
+ */
+int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_elec,
+                             const int *walker_offsets, int n_walkers, void *values,
+                             void *grads, void *laps, void *stream);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,8 @@ F32, BF16, F16, C64, BF16PAIR = 0, 1, 2, 3, 4
 NORM_BSPLINE, NORM_ALFE_GILLAN = 0, 1
 STATUS_NONFINITE_POS, STATUS_FAR_POS, STATUS_BAD_OFFSETS, STATUS_TIMEOUT = 1, 2, 4, 8
 ERRORS = {0: "ok", -1: "invalid argument", -2: "singular lattice", -3: "out of memory",
-          -4: "CUDA error", -5: "unsupported storage kind", -6: "no sm_103 CUDA device"}
+          -4: "CUDA error", -5: "unsupported storage kind", -6: "no sm_103 CUDA device",
+          -7: "batch too large for the fixed no-allocation scratch"}
 
 P = ctypes.c_void_p
 I = ctypes.c_int
@@ -42,6 +43,7 @@ EXPORTED = {
     "blip_graph_create": (I, [P, P, I, P, I, P, P, P, I, ctypes.POINTER(P)]),
     "blip_graph_launch": (I, [P, P]),
     "blip_graph_destroy": (I, [P]),
+    "blip_eval_sorted_noalloc": (I, [P, P, I, P, I, P, P, P, P]),
 }
 
 _lock = threading.Lock()

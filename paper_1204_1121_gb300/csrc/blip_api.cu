@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -352,6 +353,8 @@ const char *blip_strerror(int code)
     case BLIP_ERR_CUDA: return "CUDA error";
     case BLIP_ERR_UNSUPPORTED_DTYPE: return "unsupported storage kind";
     case BLIP_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    case BLIP_ERR_SCRATCH_LIMIT:
+        return "batch needs more sort scratch than the fixed no-allocation buffer holds";
     default: return "unknown error";
     }
 }
@@ -604,3 +607,93 @@ int blip_graph_destroy(blip_graph g)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Evaluation without any allocation: the sorted evaluation path with its sort
+// scratch taken from a fixed device array compiled into this library.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB per device
+constexpr int kNoAllocMaxDevices = 64;
+
+// The fixed scratch buffer.  Every device that loads this library holds one
+// copy until the process exits.  Host code must not use this name as an
+// address: it is a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the fixed buffer on the current device, looked up once
+// per device (the first call may load this library's module on that device).
+int noalloc_scratch(void **out)
+{
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return BLIP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return BLIP_OK;
+}
+
+}  // namespace
+
+extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_elec,
+                                        const int *walker_offsets, int n_walkers, void *values,
+                                        void *grads, void *laps, void *stream)
+{
+    int rc = validate_eval(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps);
+    if (rc) return rc;
+    if (n_elec == 0) return BLIP_OK;
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != t->device) return BLIP_ERR_INVALID_ARG;      // the table's device must be current
+    if (sort_scratch_bytes(n_elec, t->geo) > kNoAllocScratchBytes) return BLIP_ERR_SCRATCH_LIMIT;
+    void *scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the sort clears its histogram itself and overwrites everything else it reads
+    int *perm = nullptr;
+    CK(launch_sort(t->geo, pos, n_elec, scratch, &perm, s));
+    const KernelChoice kc = pick(t, n_elec);
+    EvalParams p{};
+    p.table = t->d_table;
+    p.scales = t->d_scales;
+    p.row_stride = t->row_stride;
+    p.Lreal = t->Lreal;
+    p.nchunk = t->nchunk;
+    p.groups = (t->nchunk + kc.chunks - 1) / kc.chunks;
+    p.items = (long long)n_elec * p.groups;
+    p.geo = t->geo;
+    p.pos = pos;
+    p.n_elec = n_elec;
+    p.perm = perm;
+    p.offsets = walker_offsets;
+    p.n_walkers = walker_offsets ? n_walkers : 0;
+    p.values = static_cast<float *>(values);
+    p.grads = static_cast<float *>(grads);
+    p.laps = static_cast<float *>(laps);
+    p.vec_out = (t->Lreal % 4 == 0) && aligned16(values) &&
+                (!grads || (aligned16(grads) && aligned16(laps)));
+    p.status = t->d_status;
+    if (kc.variant == VAR_BULK) {
+        const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
+        int per_sm = (int)((228 * 1024) / (smem + 1024));
+        per_sm = std::max(1, std::min(per_sm, 4));
+        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, s));
+    } else {
+        CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, s));
+    }
+    t->last_stream = s;
+    t->used = true;
+    return BLIP_OK;
+}

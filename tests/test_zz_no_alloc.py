@@ -1,0 +1,93 @@
+"""blip_eval_sorted_noalloc: evaluation that allocates nothing.
+
+Callers that record their Monte Carlo step into a CUDA graph, or that give
+all device memory to their own pool and run on a fixed budget, cannot let
+the library call cudaMalloc in the middle of a step.  This entry point takes
+the spatial sort's scratch from a fixed device buffer inside the library.
+These tests call it through the C ABI and check it against blip_eval (the
+allocating entry point) within the parity tolerance used everywhere else
+(8e-6 x sum_s |W||a| per output), on two calls in a row with different
+batches - the buffer keeps the previous call's contents, so the second call
+shows the call clears what it must.
+
+This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import blip_inputs as bi
+import oracle
+import pins
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TAU32 = 8e-6
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1204_1121_gb300 as pb
+    return pb
+
+
+def _noalloc(pb, table, pos, offs, out, values_only=False):
+    v, g, lp = out
+    nw = 0 if offs is None else offs.shape[0] - 1
+    return pb.lib().blip_eval_sorted_noalloc(
+        table.handle, ctypes.c_void_p(pos.data_ptr()), pos.shape[0],
+        ctypes.c_void_p(offs.data_ptr()) if offs is not None else None, nw,
+        ctypes.c_void_p(v.data_ptr()),
+        None if values_only else ctypes.c_void_p(g.data_ptr()),
+        None if values_only else ctypes.c_void_p(lp.data_ptr()),
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_matches_blip_eval_on_two_calls_in_a_row(pb):
+    grid = (20, 18, 16)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 300, seed=21)
+    t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
+    batches = []
+    pos_a, offs_a = bi.walker_positions(lat, 7, 600, [400, 600, 350, 500, 1, 600, 549], seed=31)
+    batches.append((pos_a, offs_a))
+    pos_b = bi.uniform_positions(lat, 1234, seed=32) - 3.0 * lat[0]
+    batches.append((pos_b, None))
+    for pos, offs in batches:
+        dpos = torch.from_numpy(pos).cuda()
+        doffs = None if offs is None else torch.from_numpy(offs).cuda()
+        ref = t.eval(dpos, doffs)                      # allocating entry point
+        out = t.alloc_outputs(len(pos))
+        for o in out:
+            o.fill_(float("nan"))
+        rc = _noalloc(pb, t, dpos, doffs, out)
+        assert rc == 0, pb.lib().blip_strerror(rc)
+        torch.cuda.synchronize()
+        _, _, _, mag = oracle.eval_stencil(grid, lat, tab, pos, absmag=True)
+        bounds = [TAU32 * mag[:, 0], TAU32 * mag[:, 1:4], TAU32 * mag[:, 4]]
+        for r, o, b in zip(ref, out, bounds):
+            diff = np.abs(o.cpu().numpy().astype(np.float64) - r.cpu().numpy())
+            assert (diff <= b + 1e-30).all()
+    assert t.status() == 0
+
+
+def test_noalloc_rejects_a_batch_beyond_the_fixed_scratch(pb):
+    grid = (20, 18, 16)
+    lat = np.diag([8.0, 7.0, 6.0])
+    tab = bi.smooth_random_table(grid, 4, seed=22)
+    t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
+    # 4 (n1 n2 n3 + 1) + 8 n_elec bytes > 8 MiB; the buffers are real and of
+    # full size, so nothing could be touched out of bounds even if the check
+    # were missing
+    n = 1_100_000
+    dpos = torch.rand((n, 3), dtype=torch.float64, device="cuda") * 6.0
+    v = torch.full((n, 4), 7.0, dtype=torch.float32, device="cuda")
+    rc = _noalloc(pb, t, dpos, None, (v, None, None), values_only=True)
+    torch.cuda.synchronize()
+    assert rc == -7
+    assert b"no-allocation" in pb.lib().blip_strerror(rc)
+    assert bool((v == 7.0).all())
