@@ -38,8 +38,8 @@ import blip_inputs as bi  # noqa: E402
 NCU_TRAFFIC = {
 }
 
-STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
-ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "c64": 3, "bf16pair": 4}
+ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2, "c64": 4, "bf16pair": 2}   # per real component
 
 
 def parse():
@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tio2",
-                    choices=["tio2", "tio2_batch", "tio2_precision", "cubic16"])
+                    choices=["tio2", "tio2_batch", "tio2_precision", "cubic16",
+                             "tio2_super_complex"])
     ap.add_argument("--batch", type=int, default=1536, help="electrons per walker (tio2_batch)")
     ap.add_argument("--walkers", type=int, default=0, help="override walker count")
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
@@ -254,10 +255,17 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = make_workload(args, rank)
-    tab = w.table()
+    if w.is_complex and args.storage in ("f32", "bf16", "f16"):
+        args.storage = "c64"
+    spectral = bool(w.extra.get("spectral"))
+    tab = w.table(device="cuda") if spectral else w.table()
     pos, offs = w.positions()
     E = len(pos)
     t = pb.BlipTable(w.grid, w.lattice, tab, storage=STORAGE[args.storage])
+    if spectral:                       # the FP64 device copy is no longer needed
+        del tab
+        tab = None
+        torch.cuda.empty_cache()
     info = t.info()
     dpos = torch.from_numpy(pos).cuda()
     doffs = torch.from_numpy(offs).cuda()
@@ -317,16 +325,31 @@ def main():
     Lr = info["Lreal"]
     bytes_alg = U * Lr * ELEM_BYTES[args.storage] + 20 * Lr * E + 24 * E
     peak, peak_kind = measured_peaks()
-    achieved = bytes_alg / (ms / 1e3) / 1e9
     kh = kernel_hash()
     rec = NCU_TRAFFIC.get((kh, w.name, args.storage, E))
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": rec,
-            "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
-            "algorithmic_bytes_per_launch": bytes_alg, "touched_sites": U,
-            "kernel_source_hash": kh,
-            "gather_model_GBps": (E * 64 * Lr * ELEM_BYTES[args.storage] + 20 * Lr * E) / (ms / 1e3) / 1e9,
-            "fp32_fma_per_launch": 320 * Lr * E}
+    # FP32 FMA peak from unit counts and clock: SMs x 128 FP32 lanes x 2 FLOP
+    # x 2.07 GHz (maximum SM clock)
+    sms = info["sm_count"]
+    f32_peak = sms * 128 * 2 * 2.07e9 / 1e12
+    flops = 640.0 * Lr * E
+    t_hbm = bytes_alg / (peak * 1e9)
+    t_alu = flops / (f32_peak * 1e12)
+    hbm_ach = bytes_alg / (ms / 1e3) / 1e9
+    alu_ach = flops / (ms / 1e3) / 1e12
+    if t_hbm >= t_alu:
+        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": peak, "unit": "GB/s",
+                "frac": hbm_ach / peak, "traffic": rec,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
+    else:
+        roof = {"bound": "alu", "achieved": alu_ach, "peak": f32_peak, "unit": "TFLOP/s",
+                "frac": alu_ach / f32_peak, "traffic": rec,
+                "peak_kind": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x 2.07 GHz"}
+    roof.update({"algorithmic_bytes_per_launch": bytes_alg, "touched_sites": U,
+                 "fp32_flop_per_launch": flops, "kernel_source_hash": kh,
+                 "hbm_frac": hbm_ach / peak, "alu_frac": alu_ach / f32_peak,
+                 "roof_time_us": 1e6 * max(t_hbm, t_alu),
+                 "gather_model_GBps": (E * 64 * Lr * ELEM_BYTES[args.storage] + 20 * Lr * E)
+                                      / (ms / 1e3) / 1e9})
 
     line = {"metric": "orbital*electron evals/s (val+grad+lap)", "value": value,
             "unit": "orbital*electron evals/s", "n_gpus": world, "steps": K,
@@ -379,7 +402,9 @@ def main():
                                  "how": "CUDA graph of 1,536 single-electron launches"}
         g.close()
 
-    if rank == 0 and not args.no_cpu_baseline:
+    if w.is_complex:
+        line["real_equivalent_value"] = 2 * value
+    if rank == 0 and not args.no_cpu_baseline and tab is not None:
         line["cpu_baseline"] = cpu_baseline(w, tab, pos, args.cpu_seconds)
 
     if rank == 0:

@@ -165,6 +165,54 @@ def smooth_random_table(grid, n_orb: int, seed: int = 0, sigma: float = 3.0,
     return out
 
 
+def spectral_table(grid, orbitals, seed: int = 0, sigma: float = 3.0, cutoff: int | None = None,
+                   device="cpu", out=None, chunk: int = 8):
+    """Smooth random COMPLEX table synthesised in Fourier space (torch).
+
+    The same statistics as ``smooth_random_table(is_complex=True)`` with a
+    cheaper recipe for large supercell grids: the DFT of complex white noise is
+    itself i.i.d. complex Gaussian, so each orbital draws N(0, 1) real and
+    imaginary parts for every mode m with |m_a| <= cutoff (default 5 sigma;
+    the Gaussian filter is below 4e-6 beyond it), multiplies mode m by
+    exp(-|m|^2 / (2 sigma^2)), inverse-FFTs on the full grid and rescales to
+    coefficient RMS 1.  ``orbitals`` is a range (or count): orbital l depends
+    only on (seed, l), so any subset of orbitals can be regenerated alone.
+    Returns (or fills ``out``) a complex128 tensor [n1][n2][n3][len(orbitals)]
+    on ``device``.
+    """
+    import torch
+    if isinstance(orbitals, int):
+        orbitals = range(orbitals)
+    grid = tuple(int(g) for g in grid)
+    K = int(cutoff if cutoff is not None else int(np.ceil(5 * sigma)))
+    ks = [min(K, (n - 1) // 2) for n in grid]
+    axes = [np.arange(-k, k + 1) for k in ks]
+    box = tuple(len(a) for a in axes)
+    M = int(np.prod(box))
+    m2 = (axes[0][:, None, None] ** 2 + axes[1][None, :, None] ** 2
+          + axes[2][None, None, :] ** 2).astype(np.float64)
+    filt = torch.from_numpy(np.exp(-m2 / (2.0 * sigma * sigma))).to(device)
+    idx = [torch.from_numpy(np.mod(a, n)).to(device) for a, n in zip(axes, grid)]
+    L = len(orbitals)
+    if out is None:
+        out = torch.empty(grid + (L,), dtype=torch.complex128, device=device)
+    key = stream_key(seed, 0x5BEC7)
+    ol = list(orbitals)
+    for c0 in range(0, L, chunk):
+        ls = ol[c0:c0 + chunk]
+        G = torch.zeros((len(ls),) + grid, dtype=torch.complex128, device=device)
+        for j, l in enumerate(ls):
+            z = torch.from_numpy(normal(key, 2 * M * l, 2 * M)).to(device)
+            F = torch.complex(z[:M], z[M:]).reshape(box) * filt
+            G[j][idx[0][:, None, None], idx[1][None, :, None], idx[2][None, None, :]] = F
+        blk = torch.fft.ifftn(G, dim=(1, 2, 3))
+        rms = torch.sqrt(torch.mean(blk.real ** 2 + blk.imag ** 2, dim=(1, 2, 3)))
+        blk /= rms[:, None, None, None]
+        out[..., c0:c0 + len(ls)] = blk.permute(1, 2, 3, 0)
+        del G, blk
+    return out
+
+
 # ---------------------------------------------------------------------------
 # positions
 # ---------------------------------------------------------------------------
@@ -243,7 +291,13 @@ class Workload:
             b = self.batch
         return walker_positions(self.lattice, self.n_walkers, self.n_per_walker, b, self.pos_seed)
 
-    def table(self, dtype=None, threads=None):
+    def table(self, dtype=None, threads=None, device="cpu", orbitals=None):
+        """The coefficient table.  Complex supercell workloads use the
+        Fourier-space recipe (``spectral_table``, a torch tensor on
+        ``device``); the others the grid-noise recipe (numpy, host)."""
+        if self.extra.get("spectral"):
+            return spectral_table(self.grid, orbitals if orbitals is not None else self.n_orb,
+                                  self.table_seed, device=device)
         return smooth_random_table(self.grid, self.n_orb, self.table_seed,
                                    is_complex=self.is_complex, dtype=dtype, threads=threads)
 
@@ -268,8 +322,8 @@ def workload(name: str, **kw) -> Workload:
       per walker (keyword ``batch``, default 1536).
     * ``tio2_precision``: the same table, 1,024 walkers x 1,536 electrons.
     * ``tio2_super_complex``: 2 x 2 x 2 supercell (34.8 x 34.8 x 22.4 bohr),
-      144 x 144 x 96 grid, 1,536 complex orbitals, 512 walkers with batch sizes
-      uniform in {1..512}.
+      144 x 144 x 96 grid, 1,536 complex orbitals (Fourier-space table
+      recipe), 512 walkers with batch sizes uniform in {1..512}.
     """
     if name == "cubic16":
         w = Workload(name, cubic_lattice(10.0), (16, 16, 16), 8, table_seed=0, pos_seed=0,
@@ -285,9 +339,10 @@ def workload(name: str, **kw) -> Workload:
         w = Workload(name, TIO2_CELL, TIO2_GRID, 768, table_seed=0, pos_seed=103,
                      n_walkers=kw.pop("n_walkers", 1024), n_per_walker=1536, batch=1536)
     elif name == "tio2_super_complex":
-        w = Workload(name, tetragonal_lattice(34.8, 22.4), (144, 144, 96), 1536,
+        w = Workload(name, tetragonal_lattice(34.8, 22.4), (144, 144, 96), kw.pop("n_orb", 1536),
                      is_complex=True, table_seed=0, pos_seed=104,
-                     n_walkers=kw.pop("n_walkers", 512), n_per_walker=512, ragged=(1, 512))
+                     n_walkers=kw.pop("n_walkers", 512), n_per_walker=512, ragged=(1, 512),
+                     extra={"spectral": True})
     else:
         raise KeyError(name)
     for k, v in kw.items():

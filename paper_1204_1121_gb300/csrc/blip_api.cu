@@ -472,7 +472,7 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         t->auto_mode = true;
         return BLIP_OK;
     }
-    if (variant == VAR_REGISTER) {
+    if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE) {
         const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
         if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
         if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
@@ -506,7 +506,10 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     tws.erase(std::unique(tws.begin(), tws.end()), tws.end());
     for (int srt = 0; srt <= (n_elec >= 4096 ? 1 : 0); ++srt) {
         for (int c = 1; c <= max_chunks; ++c)
-            for (int w : {4, 8, 16}) cands.push_back(KernelChoice{VAR_REGISTER, c, w, srt});
+            for (int w : {4, 8, 16}) {
+                cands.push_back(KernelChoice{VAR_REGISTER, c, w, srt});
+                cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, srt});
+            }
         for (int tw : tws)
             for (int st : {4, 8, 16})
                 if (bulk_smem_bytes(tw, st) <= 227 * 1024)

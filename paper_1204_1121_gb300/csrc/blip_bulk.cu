@@ -182,7 +182,6 @@ __global__ void __launch_bounds__(288) blip_eval_bulk(EvalParams p, BulkArgs b)
                         d.pad[0] = d.pad[1] = d.pad[2] = 0;
                         desc[s] = d;
                     }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_expect_tx(full + s, 4u * piece);
                     unsigned char *dst = stage0 + (size_t)s * b.stage_bytes;
                     const char *src = tbase + (size_t)row * row_bytes + (size_t)c0 * 512u;

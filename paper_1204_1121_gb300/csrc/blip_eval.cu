@@ -72,7 +72,7 @@ __device__ __forceinline__ void store_outputs(const EvalParams &p, int e, int gr
 // Register-gather kernel: each lane loads its 16-byte slices of the 64 rows
 // straight into registers (4 columns = 16 rows in flight per batch for one
 // chunk, fewer for more chunks).
-template <typename T, int CPW, bool VONLY>
+template <typename T, int CPW, bool VONLY, bool PIPE>
 __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 {
     constexpr int VEC = Elt<T>::VEC;
@@ -124,29 +124,39 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
             coff[c] = ((size_t)chunk * 32 * VEC + (size_t)lane * VEC) * sizeof(T);
         }
 
-#pragma unroll 1
-        for (int c0 = 0; c0 < 16; c0 += COLS) {
-            uint4 raw[COLS][4][CPW];
+        if constexpr (PIPE) {
+            // software-pipelined: the next batch of RB rows is in flight while
+            // the current batch is contracted (two register buffers)
+            constexpr int RB = CPW == 1 ? 8 : (CPW == 2 ? 4 : 2);
+            constexpr int NB = 64 / RB;
+            uint4 buf[2][RB][CPW];
 #pragma unroll
-            for (int cc = 0; cc < COLS; ++cc) {
-                const char *rp = tbase + (size_t)ws.colrow[c0 + cc] * rowb;
+            for (int r = 0; r < RB; ++r) {
+                const char *rp = tbase + (size_t)(ws.colrow[r >> 2] + (r & 3)) * rowb;
 #pragma unroll
-                for (int kz = 0; kz < 4; ++kz)
-#pragma unroll
-                    for (int c = 0; c < CPW; ++c)
-                        raw[cc][kz][c] = ldg_stream(rp + kz * rowb + coff[c]);
+                for (int c = 0; c < CPW; ++c) buf[0][r][c] = ldg_stream(rp + coff[c]);
             }
 #pragma unroll
-            for (int cc = 0; cc < COLS; ++cc)
+            for (int b = 0; b < NB; ++b) {
+                if (b + 1 < NB) {
 #pragma unroll
-                for (int kz = 0; kz < 4; ++kz) {
-                    const int pt = (c0 + cc) * 4 + kz;
+                    for (int r = 0; r < RB; ++r) {
+                        const int pt = (b + 1) * RB + r;
+                        const char *rp = tbase + (size_t)(ws.colrow[pt >> 2] + (pt & 3)) * rowb;
+#pragma unroll
+                        for (int c = 0; c < CPW; ++c)
+                            buf[(b + 1) & 1][r][c] = ldg_stream(rp + coff[c]);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int pt = b * RB + r;
                     const float4 w = ws.w4[pt];
                     const float wl = VONLY ? 0.0f : ws.wl[pt];
 #pragma unroll
                     for (int c = 0; c < CPW; ++c) {
                         float f[VEC];
-                        Elt<T>::unpack(raw[cc][kz][c], f);
+                        Elt<T>::unpack(buf[b & 1][r][c], f);
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
                             acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
@@ -159,42 +169,86 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                         }
                     }
                 }
+            }
+        } else {
+    #pragma unroll 1
+            for (int c0 = 0; c0 < 16; c0 += COLS) {
+                uint4 raw[COLS][4][CPW];
+    #pragma unroll
+                for (int cc = 0; cc < COLS; ++cc) {
+                    const char *rp = tbase + (size_t)ws.colrow[c0 + cc] * rowb;
+    #pragma unroll
+                    for (int kz = 0; kz < 4; ++kz)
+    #pragma unroll
+                        for (int c = 0; c < CPW; ++c)
+                            raw[cc][kz][c] = ldg_stream(rp + kz * rowb + coff[c]);
+                }
+    #pragma unroll
+                for (int cc = 0; cc < COLS; ++cc)
+    #pragma unroll
+                    for (int kz = 0; kz < 4; ++kz) {
+                        const int pt = (c0 + cc) * 4 + kz;
+                        const float4 w = ws.w4[pt];
+                        const float wl = VONLY ? 0.0f : ws.wl[pt];
+    #pragma unroll
+                        for (int c = 0; c < CPW; ++c) {
+                            float f[VEC];
+                            Elt<T>::unpack(raw[cc][kz][c], f);
+    #pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
+                                if constexpr (!VONLY) {
+                                    acc[c][1][v] = fmaf(w.y, f[v], acc[c][1][v]);
+                                    acc[c][2][v] = fmaf(w.z, f[v], acc[c][2][v]);
+                                    acc[c][3][v] = fmaf(w.w, f[v], acc[c][3][v]);
+                                    acc[c][4][v] = fmaf(wl, f[v], acc[c][4][v]);
+                                }
+                            }
+                        }
+                    }
+            }
         }
         store_outputs<CPW, VEC, VONLY>(p, e, grp, lane, acc);
     }
 }
 
 template <typename T, int CPW, bool VONLY>
-cudaError_t launch_register_t(const EvalParams &p, int warps, cudaStream_t stream)
+cudaError_t launch_register_t(const EvalParams &p, int warps, bool pipe, cudaStream_t stream)
 {
     const size_t smem = sizeof(WarpSlice) * (size_t)warps;
     long long blocks = (p.items + warps - 1) / warps;
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    blip_eval_register<T, CPW, VONLY><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
+    if (pipe)
+        blip_eval_register<T, CPW, VONLY, true><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
+    else
+        blip_eval_register<T, CPW, VONLY, false><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
 template <typename T, bool VONLY>
-cudaError_t launch_register_c(const EvalParams &p, int chunks, int warps, cudaStream_t stream)
+cudaError_t launch_register_c(const EvalParams &p, int chunks, int warps, bool pipe,
+                              cudaStream_t stream)
 {
     if constexpr (sizeof(T) == 2) {        // 16-bit elements: one chunk per warp
         if (chunks != 1) return cudaErrorInvalidValue;
-        return launch_register_t<T, 1, VONLY>(p, warps, stream);
-    }
-    switch (chunks) {
-    case 1: return launch_register_t<T, 1, VONLY>(p, warps, stream);
-    case 2: return launch_register_t<T, 2, VONLY>(p, warps, stream);
-    case 3: return launch_register_t<T, 3, VONLY>(p, warps, stream);
-    default: return cudaErrorInvalidValue;
+        return launch_register_t<T, 1, VONLY>(p, warps, pipe, stream);
+    } else {
+        switch (chunks) {
+        case 1: return launch_register_t<T, 1, VONLY>(p, warps, pipe, stream);
+        case 2: return launch_register_t<T, 2, VONLY>(p, warps, pipe, stream);
+        case 3: return launch_register_t<T, 3, VONLY>(p, warps, pipe, stream);
+        default: return cudaErrorInvalidValue;
+        }
     }
 }
 
 template <typename T>
-cudaError_t launch_register(const EvalParams &p, int chunks, int warps, cudaStream_t stream)
+cudaError_t launch_register(const EvalParams &p, int chunks, int warps, bool pipe,
+                            cudaStream_t stream)
 {
-    if (p.grads) return launch_register_c<T, false>(p, chunks, warps, stream);
-    return launch_register_c<T, true>(p, chunks, warps, stream);
+    if (p.grads) return launch_register_c<T, false>(p, chunks, warps, pipe, stream);
+    return launch_register_c<T, true>(p, chunks, warps, pipe, stream);
 }
 
 }  // namespace
@@ -203,11 +257,12 @@ cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, 
                         cudaStream_t stream)
 {
     if (warps < 1 || warps > 16) return cudaErrorInvalidValue;
-    if (variant != VAR_REGISTER) return cudaErrorInvalidValue;
+    if (variant != VAR_REGISTER && variant != VAR_REGISTER_PIPE) return cudaErrorInvalidValue;
+    const bool pipe = variant == VAR_REGISTER_PIPE;
     switch (elem) {
-    case ELEM_F32: return launch_register<float>(p, chunks, warps, stream);
-    case ELEM_BF16: return launch_register<__nv_bfloat16>(p, chunks, warps, stream);
-    case ELEM_F16: return launch_register<__half>(p, chunks, warps, stream);
+    case ELEM_F32: return launch_register<float>(p, chunks, warps, pipe, stream);
+    case ELEM_BF16: return launch_register<__nv_bfloat16>(p, chunks, warps, pipe, stream);
+    case ELEM_F16: return launch_register<__half>(p, chunks, warps, pipe, stream);
     default: return cudaErrorInvalidValue;
     }
 }

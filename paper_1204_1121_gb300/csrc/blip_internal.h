@@ -11,7 +11,7 @@ namespace blip {
 enum Elem { ELEM_F32 = 0, ELEM_BF16 = 1, ELEM_F16 = 2 };
 
 // Kernel variants.
-enum Variant { VAR_AUTO = 0, VAR_REGISTER = 1, VAR_BULK = 2 };
+enum Variant { VAR_AUTO = 0, VAR_REGISTER = 1, VAR_BULK = 2, VAR_REGISTER_PIPE = 3 };
 
 // Cell geometry, prepared once on the host in FP64.
 struct Geometry {
@@ -49,8 +49,9 @@ struct EvalParams {
 inline int elem_vec(int elem) { return elem == ELEM_F32 ? 4 : 8; }
 inline int elem_bytes(int elem) { return elem == ELEM_F32 ? 4 : 2; }
 
-// Launch the register-gather kernel.  chunks in {1, 2, 3} (1 for 16-bit
-// elements); warps in [1, 16].
+// Launch the register-gather kernel (variant VAR_REGISTER, or
+// VAR_REGISTER_PIPE for the software-pipelined loop).  chunks in {1, 2, 3}
+// (1 for 16-bit elements); warps in [1, 16].
 cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, int warps,
                         cudaStream_t stream);
 

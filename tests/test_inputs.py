@@ -66,3 +66,29 @@ def test_named_workloads():
     w = bi.workload("tio2_batch", batch=8)
     p, offs = w.positions()
     assert p.shape == (256 * 8, 3) and offs[-1] == 2048
+
+
+def test_spectral_table_orbitals_are_independent_and_normalised():
+    torch = __import__("pytest").importorskip("torch")
+    a = bi.spectral_table((12, 10, 8), 5, seed=4, sigma=1.5, chunk=2)
+    b = bi.spectral_table((12, 10, 8), range(3, 5), seed=4, sigma=1.5, chunk=1)
+    assert a.shape == (12, 10, 8, 5) and a.dtype == torch.complex128
+    assert torch.allclose(a[..., 3:5], b, rtol=0, atol=1e-13)
+    rms = torch.sqrt((a.abs() ** 2).mean(dim=(0, 1, 2)))
+    assert torch.allclose(rms, torch.ones(5, dtype=torch.float64))
+    # smooth: lag-1 correlation along the 12-point axis is high
+    c = (a * torch.roll(a, 1, dims=0).conj()).real.mean().item()
+    assert c > 0.5
+
+
+def test_spectral_table_matches_the_gaussian_filter_spectrum():
+    """The power spectrum of the table falls off as exp(-|m|^2 / sigma^2)."""
+    a = bi.spectral_table((24, 24, 24), 16, seed=9, sigma=3.0).numpy()
+    f = np.fft.fftn(a, axes=(0, 1, 2))
+    pw = (np.abs(f) ** 2).mean(axis=-1)
+    m = np.fft.fftfreq(24) * 24
+    r0 = pw[0, 0, 0]
+    for k in (2, 4):
+        expect = np.exp(-(k * k) / 9.0)
+        got = np.mean([pw[k, 0, 0], pw[-k, 0, 0], pw[0, k, 0], pw[0, 0, k]]) / r0
+        assert 0.3 * expect < got < 3.0 * expect
