@@ -95,7 +95,9 @@ typedef struct blip_graph_s *blip_graph;
  *   coeffs_on_device  0: coeffs is a host pointer; 1: a device pointer
  *   out               receives the handle
  * Ownership: the library copies (and converts / quantises) the coefficients
- * into memory it owns; the caller keeps and frees its buffer.  The call
+ * into memory it owns; the caller keeps and frees its buffer.  For a device
+ * source the call first waits for all work queued on the device (so a buffer
+ * still being produced on any stream is complete before it is read), and it
  * synchronises the device before returning.  Errors: INVALID_ARG,
  * SINGULAR_LATTICE, UNSUPPORTED_DTYPE, OOM, CUDA, NO_DEVICE; *out is NULL on
  * error.
@@ -188,6 +190,30 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort);
 int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
                   int n_walkers, void *values, void *grads, void *laps, void *stream,
                   int chosen[4]);
+
+/*
+ * blip_eval_ratio - fused quasi-simultaneous ratio (real orbitals).
+ *
+ * For the trial move r'_j of each electron (Sec. IV.A, Eq. 11.12.23.1) the
+ * determinant ratio is the new orbital row dotted with column j of the
+ * inverse Slater matrix, xi_j = sum_l psi_l(r'_j) (D^{-1})_{lj} (the
+ * identity behind the Sherman-Morrison update, Sec. VI.D); the drift and
+ * kinetic terms need the same contraction of the gradient and Laplacian.
+ * This call evaluates the orbitals (Eq. 11.12.24.1) and contracts them on the
+ * chip, writing five numbers per electron instead of 5 n_orb:
+ *   inv_cols   device [n_elec][n_orb] float: for electron j, the column
+ *              (D^{-1})_{. j} of its own walker's and spin's inverse
+ *   ratio      device [n_elec][5] float: sum_l {psi, d/dx psi, d/dy psi,
+ *              d/dz psi, lap psi}_l(r'_j) inv_cols[j][l]
+ *   values     device [n_elec][n_orb] float for the new rows psi_l(r'_j)
+ *              (needed to update D^{-1} after an accepted move), or NULL
+ *   sort       0: input order; 1: evaluate in grid-cell order (same results)
+ * Other arguments as blip_eval.  Deterministic (fixed reduction order).
+ * Errors: INVALID_ARG, UNSUPPORTED_DTYPE (complex tables), CUDA.
+ */
+int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+                    int n_walkers, const float *inv_cols, float *ratio, float *values, int sort,
+                    void *stream);
 
 /*
  * blip_graph_create - capture a fixed evaluation into a CUDA graph.

@@ -44,6 +44,7 @@ EXPORTED = {
     "blip_graph_launch": (I, [P, P]),
     "blip_graph_destroy": (I, [P]),
     "blip_eval_sorted_noalloc": (I, [P, P, I, P, I, P, P, P, P]),
+    "blip_eval_ratio": (I, [P, P, I, P, I, P, P, P, I, P]),
 }
 
 _lock = threading.Lock()
@@ -219,6 +220,27 @@ class BlipTable:
                                         P(ptr(g)) if g is not None else None,
                                         P(ptr(lp)) if lp is not None else None), "blip_eval_host")
         return v, g, lp
+
+    def eval_ratio(self, pos, inv_cols, offsets=None, with_values=False, sort=0, stream=None):
+        """Fused ratio (``blip_eval_ratio``): returns (ratio [E][5], values or
+        None).  ``inv_cols``: CUDA float32 [E][n_orb], column j of the inverse
+        Slater matrix for electron j."""
+        import torch
+        if not (pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous()):
+            raise TypeError("pos must be a contiguous CUDA float64 tensor")
+        if not (inv_cols.is_cuda and inv_cols.dtype == torch.float32 and inv_cols.is_contiguous()):
+            raise TypeError("inv_cols must be a contiguous CUDA float32 tensor")
+        n = pos.shape[0]
+        ratio = torch.empty((n, 5), dtype=torch.float32, device=pos.device)
+        vals = torch.empty((n, self.Lreal), dtype=torch.float32, device=pos.device) \
+            if with_values else None
+        nw = 0 if offsets is None else offsets.shape[0] - 1
+        _check(self._lib.blip_eval_ratio(self._h, P(pos.data_ptr()), n,
+                                         P(offsets.data_ptr()) if offsets is not None else None,
+                                         nw, P(inv_cols.data_ptr()), P(ratio.data_ptr()),
+                                         P(vals.data_ptr()) if vals is not None else None,
+                                         int(sort), _stream_ptr(stream)), "blip_eval_ratio")
+        return ratio, vals
 
     def status(self):
         s = ctypes.c_int(0)

@@ -156,6 +156,28 @@ int validate_eval(const blip_table_s *t, const double *pos, int n_elec, const in
     return BLIP_OK;
 }
 
+// Spatial sort of the batch into the table's scratch (grown outside stream
+// capture); *perm receives the evaluation order.
+int sorted_order(blip_table_s *t, const double *pos, int n_elec, cudaStream_t stream, int **perm)
+{
+    const size_t need = sort_scratch_bytes(n_elec, t->geo);
+    if (t->scratch_bytes < need) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(stream, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return BLIP_ERR_INVALID_ARG;  // no growth in capture
+        if (t->scratch) {
+            CK(cudaStreamSynchronize(t->last_stream));
+            cudaFree(t->scratch);
+        }
+        t->scratch = nullptr;
+        t->scratch_bytes = 0;
+        CK(cudaMalloc(&t->scratch, need));
+        t->scratch_bytes = need;
+    }
+    CK(launch_sort(t->geo, pos, n_elec, t->scratch, perm, stream));
+    return BLIP_OK;
+}
+
 int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs, int n_walkers,
                 void *values, void *grads, void *laps, cudaStream_t stream, const KernelChoice &kc)
 {
@@ -173,22 +195,9 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
     p.n_elec = n_elec;
     p.perm = nullptr;
     if (kc.sort) {
-        const size_t need = sort_scratch_bytes(n_elec, t->geo);
-        if (t->scratch_bytes < need) {
-            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-            CK(cudaStreamIsCapturing(stream, &cs));
-            if (cs != cudaStreamCaptureStatusNone) return BLIP_ERR_INVALID_ARG;  // no growth in capture
-            if (t->scratch) {
-                CK(cudaStreamSynchronize(t->last_stream));
-                cudaFree(t->scratch);
-            }
-            t->scratch = nullptr;
-            t->scratch_bytes = 0;
-            CK(cudaMalloc(&t->scratch, need));
-            t->scratch_bytes = need;
-        }
         int *perm = nullptr;
-        CK(launch_sort(t->geo, pos, n_elec, t->scratch, &perm, stream));
+        int rc = sorted_order(t, pos, n_elec, stream, &perm);
+        if (rc) return rc;
         p.perm = perm;
     }
     p.offsets = offs;
@@ -276,6 +285,10 @@ int create_impl(const int grid[3], const double lattice[9], int n_orb, int stora
 
     CK(cudaStreamCreateWithFlags(&t->own_stream, cudaStreamNonBlocking));
     cudaStream_t s = t->own_stream;
+    // A device source may still be being written by work the caller queued on
+    // any stream (the library's stream does not order after the legacy
+    // default stream): wait for the whole device before reading it.
+    if (coeffs_on_device) CK(cudaDeviceSynchronize());
     CK(cudaMalloc(&t->d_status, sizeof(int)));
     CK(cudaMemsetAsync(t->d_status, 0, sizeof(int), s));
 
@@ -472,7 +485,7 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         t->auto_mode = true;
         return BLIP_OK;
     }
-    if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE) {
+    if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE || variant == VAR_REGISTER_ROLLED) {
         const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
         if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
         if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
@@ -509,6 +522,7 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
             for (int w : {4, 8, 16}) {
                 cands.push_back(KernelChoice{VAR_REGISTER, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, srt});
+                cands.push_back(KernelChoice{VAR_REGISTER_ROLLED, c, w, srt});
             }
         for (int tw : tws)
             for (int st : {4, 8, 16})
@@ -548,6 +562,47 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
         chosen[2] = bestc.warps;
         chosen[3] = bestc.sort;
     }
+    return BLIP_OK;
+}
+
+int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
+                    int n_walkers, const float *inv_cols, float *ratio, float *values, int sort,
+                    void *stream)
+{
+    if (!t || n_elec < 0 || (walker_offsets && n_walkers < 1)) return BLIP_ERR_INVALID_ARG;
+    if (n_elec > 0 && (!pos || !inv_cols || !ratio)) return BLIP_ERR_INVALID_ARG;
+    if (t->is_complex) return BLIP_ERR_UNSUPPORTED_DTYPE;
+    if (sort != 0 && sort != 1) return BLIP_ERR_INVALID_ARG;
+    if (n_elec == 0) return BLIP_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EvalParams p{};
+    p.table = t->d_table;
+    p.scales = t->d_scales;
+    p.row_stride = t->row_stride;
+    p.Lreal = t->Lreal;
+    p.nchunk = t->nchunk;
+    p.groups = 1;
+    p.items = n_elec;
+    p.geo = t->geo;
+    p.pos = pos;
+    p.n_elec = n_elec;
+    p.perm = nullptr;
+    if (sort) {
+        int *perm = nullptr;
+        int rc = sorted_order(t, pos, n_elec, s, &perm);
+        if (rc) return rc;
+        p.perm = perm;
+    }
+    p.offsets = walker_offsets;
+    p.n_walkers = walker_offsets ? n_walkers : 0;
+    p.values = values;
+    p.grads = nullptr;
+    p.laps = nullptr;
+    p.vec_out = 0;
+    p.status = t->d_status;
+    CK(launch_ratio(p, t->elem, inv_cols, ratio, 4, s));
+    t->last_stream = s;
+    t->used = true;
     return BLIP_OK;
 }
 

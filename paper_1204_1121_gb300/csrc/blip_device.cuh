@@ -169,6 +169,33 @@ __device__ __forceinline__ int column_row(const Geometry &geo, int i0, int i1, i
     return (ix * n2 + iy) * (n3 + 3) + i2;
 }
 
+// Steps 1-2 for electron e: FP64 wrap on lanes 0-2, then weights and column
+// rows into the warp's slice.  Returns the warp-uniform status bits.
+__device__ __forceinline__ int stencil_setup_warp(const EvalParams &p, int e, int lane,
+                                                  WarpSlice &ws)
+{
+    int ia = 0, bad = 0;
+    float ta = 0.0f;
+    if (lane < 3) {
+        const double *r = p.pos + 3 * (size_t)e;
+        bad = wrap_axis(p.geo, lane, r[0], r[1], r[2], ia, ta);
+    }
+    bad = __reduce_or_sync(FULL, bad);
+    const int i0 = __shfl_sync(FULL, ia, 0), i1 = __shfl_sync(FULL, ia, 1),
+              i2 = __shfl_sync(FULL, ia, 2);
+    const float t0 = __shfl_sync(FULL, ta, 0), t1 = __shfl_sync(FULL, ta, 1),
+                t2 = __shfl_sync(FULL, ta, 2);
+    if (bad & BLIP_STATUS_NONFINITE_POS) return bad;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int pt = lane + 32 * h;
+        site_weights(p.geo, t0, t1, t2, pt, ws.w4[pt], ws.wl[pt]);
+    }
+    if (lane < 16) ws.colrow[lane] = column_row(p.geo, i0, i1, i2, lane);
+    __syncwarp();
+    return bad;
+}
+
 // Scale (quantised tables) and write the five outputs of one chunk
 // (32 lanes x VEC components) of electron e with streaming stores.
 template <int VEC, bool VONLY>

@@ -31,32 +31,6 @@ namespace {
 
 using namespace dev;
 
-// Steps 1-2 for electron e: FP64 wrap on lanes 0-2, then weights and column
-// rows into the warp's slice.  Returns the warp-uniform status bits.
-__device__ __forceinline__ int stencil_setup(const EvalParams &p, int e, int lane, WarpSlice &ws)
-{
-    int ia = 0, bad = 0;
-    float ta = 0.0f;
-    if (lane < 3) {
-        const double *r = p.pos + 3 * (size_t)e;
-        bad = wrap_axis(p.geo, lane, r[0], r[1], r[2], ia, ta);
-    }
-    bad = __reduce_or_sync(FULL, bad);
-    const int i0 = __shfl_sync(FULL, ia, 0), i1 = __shfl_sync(FULL, ia, 1),
-              i2 = __shfl_sync(FULL, ia, 2);
-    const float t0 = __shfl_sync(FULL, ta, 0), t1 = __shfl_sync(FULL, ta, 1),
-                t2 = __shfl_sync(FULL, ta, 2);
-    if (bad & BLIP_STATUS_NONFINITE_POS) return bad;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int pt = lane + 32 * h;
-        site_weights(p.geo, t0, t1, t2, pt, ws.w4[pt], ws.wl[pt]);
-    }
-    if (lane < 16) ws.colrow[lane] = column_row(p.geo, i0, i1, i2, lane);
-    __syncwarp();
-    return bad;
-}
-
 template <int CPW, int VEC, bool VONLY>
 __device__ __forceinline__ void store_outputs(const EvalParams &p, int e, int grp, int lane,
                                               float (&acc)[CPW][VONLY ? 1 : 5][VEC])
@@ -69,10 +43,39 @@ __device__ __forceinline__ void store_outputs(const EvalParams &p, int e, int gr
     }
 }
 
+// Contract RB rows (stencil sites pt0 .. pt0 + RB - 1) held in registers
+// into the accumulators: 5 FMAs per component per row.
+template <typename T, int CPW, int VEC, bool VONLY, int RB>
+__device__ __forceinline__ void contract_rows(const WarpSlice &ws, int pt0,
+                                              const uint4 (&buf)[RB][CPW],
+                                              float (&acc)[CPW][VONLY ? 1 : 5][VEC])
+{
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        const float4 w = ws.w4[pt0 + r];
+        const float wl = VONLY ? 0.0f : ws.wl[pt0 + r];
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+            float f[VEC];
+            Elt<T>::unpack(buf[r][c], f);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
+                if constexpr (!VONLY) {
+                    acc[c][1][v] = fmaf(w.y, f[v], acc[c][1][v]);
+                    acc[c][2][v] = fmaf(w.z, f[v], acc[c][2][v]);
+                    acc[c][3][v] = fmaf(w.w, f[v], acc[c][3][v]);
+                    acc[c][4][v] = fmaf(wl, f[v], acc[c][4][v]);
+                }
+            }
+        }
+    }
+}
+
 // Register-gather kernel: each lane loads its 16-byte slices of the 64 rows
 // straight into registers (4 columns = 16 rows in flight per batch for one
 // chunk, fewer for more chunks).
-template <typename T, int CPW, bool VONLY, bool PIPE>
+template <typename T, int CPW, bool VONLY, int PIPE>
 __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 {
     constexpr int VEC = Elt<T>::VEC;
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                 for (int v = 0; v < VEC; ++v) acc[c][k][v] = 0.0f;
 
         __syncwarp();                      // previous item's readers are done with the slice
-        const int bad = stencil_setup(p, e, lane, ws);
+        const int bad = stencil_setup_warp(p, e, lane, ws);
         if (bad && lane == 0) atomicOr(p.status, bad);
         if (bad & BLIP_STATUS_NONFINITE_POS) {
 #pragma unroll
@@ -124,7 +127,41 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
             coff[c] = ((size_t)chunk * 32 * VEC + (size_t)lane * VEC) * sizeof(T);
         }
 
-        if constexpr (PIPE) {
+        if constexpr (PIPE == 2) {
+            // software-pipelined with a rolled loop over pairs of batches
+            // (smaller code: the fully unrolled form misses in the instruction
+            // cache when three chunks are in flight)
+            constexpr int RB = CPW == 1 ? 4 : (CPW == 2 ? 2 : 1);
+            constexpr int NB = 64 / RB;
+            uint4 b0[RB][CPW], b1[RB][CPW];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const char *rp = tbase + (size_t)(ws.colrow[r >> 2] + (r & 3)) * rowb;
+#pragma unroll
+                for (int c = 0; c < CPW; ++c) b0[r][c] = ldg_stream(rp + coff[c]);
+            }
+#pragma unroll 1
+            for (int b = 0; b < NB; b += 2) {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int pt = (b + 1) * RB + r;
+                    const char *rp = tbase + (size_t)(ws.colrow[pt >> 2] + (pt & 3)) * rowb;
+#pragma unroll
+                    for (int c = 0; c < CPW; ++c) b1[r][c] = ldg_stream(rp + coff[c]);
+                }
+                contract_rows<T, CPW, VEC, VONLY, RB>(ws, b * RB, b0, acc);
+                if (b + 2 < NB) {
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        const int pt = (b + 2) * RB + r;
+                        const char *rp = tbase + (size_t)(ws.colrow[pt >> 2] + (pt & 3)) * rowb;
+#pragma unroll
+                        for (int c = 0; c < CPW; ++c) b0[r][c] = ldg_stream(rp + coff[c]);
+                    }
+                }
+                contract_rows<T, CPW, VEC, VONLY, RB>(ws, (b + 1) * RB, b1, acc);
+            }
+        } else if constexpr (PIPE == 1) {
             // software-pipelined: the next batch of RB rows is in flight while
             // the current batch is contracted (two register buffers)
             constexpr int RB = CPW == 1 ? 8 : (CPW == 2 ? 4 : 2);
@@ -213,21 +250,23 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 }
 
 template <typename T, int CPW, bool VONLY>
-cudaError_t launch_register_t(const EvalParams &p, int warps, bool pipe, cudaStream_t stream)
+cudaError_t launch_register_t(const EvalParams &p, int warps, int pipe, cudaStream_t stream)
 {
     const size_t smem = sizeof(WarpSlice) * (size_t)warps;
     long long blocks = (p.items + warps - 1) / warps;
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    if (pipe)
-        blip_eval_register<T, CPW, VONLY, true><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
+    if (pipe == 2)
+        blip_eval_register<T, CPW, VONLY, 2><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
+    else if (pipe == 1)
+        blip_eval_register<T, CPW, VONLY, 1><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
     else
-        blip_eval_register<T, CPW, VONLY, false><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
+        blip_eval_register<T, CPW, VONLY, 0><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
 template <typename T, bool VONLY>
-cudaError_t launch_register_c(const EvalParams &p, int chunks, int warps, bool pipe,
+cudaError_t launch_register_c(const EvalParams &p, int chunks, int warps, int pipe,
                               cudaStream_t stream)
 {
     if constexpr (sizeof(T) == 2) {        // 16-bit elements: one chunk per warp
@@ -244,7 +283,7 @@ cudaError_t launch_register_c(const EvalParams &p, int chunks, int warps, bool p
 }
 
 template <typename T>
-cudaError_t launch_register(const EvalParams &p, int chunks, int warps, bool pipe,
+cudaError_t launch_register(const EvalParams &p, int chunks, int warps, int pipe,
                             cudaStream_t stream)
 {
     if (p.grads) return launch_register_c<T, false>(p, chunks, warps, pipe, stream);
@@ -257,8 +296,9 @@ cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, 
                         cudaStream_t stream)
 {
     if (warps < 1 || warps > 16) return cudaErrorInvalidValue;
-    if (variant != VAR_REGISTER && variant != VAR_REGISTER_PIPE) return cudaErrorInvalidValue;
-    const bool pipe = variant == VAR_REGISTER_PIPE;
+    if (variant != VAR_REGISTER && variant != VAR_REGISTER_PIPE && variant != VAR_REGISTER_ROLLED)
+        return cudaErrorInvalidValue;
+    const int pipe = variant == VAR_REGISTER_PIPE ? 1 : (variant == VAR_REGISTER_ROLLED ? 2 : 0);
     switch (elem) {
     case ELEM_F32: return launch_register<float>(p, chunks, warps, pipe, stream);
     case ELEM_BF16: return launch_register<__nv_bfloat16>(p, chunks, warps, pipe, stream);

@@ -11,7 +11,13 @@ namespace blip {
 enum Elem { ELEM_F32 = 0, ELEM_BF16 = 1, ELEM_F16 = 2 };
 
 // Kernel variants.
-enum Variant { VAR_AUTO = 0, VAR_REGISTER = 1, VAR_BULK = 2, VAR_REGISTER_PIPE = 3 };
+enum Variant {
+    VAR_AUTO = 0,
+    VAR_REGISTER = 1,         // batches of 16 rows, loads then contraction
+    VAR_BULK = 2,             // bulk-copy producer/consumer pipeline
+    VAR_REGISTER_PIPE = 3,    // double-buffered batches, fully unrolled
+    VAR_REGISTER_ROLLED = 4   // double-buffered batches, rolled loop
+};
 
 // Cell geometry, prepared once on the host in FP64.
 struct Geometry {
@@ -60,6 +66,12 @@ cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, 
 cudaError_t launch_bulk(const EvalParams &p, int elem, int tw, int stages, int ctas_per_sm,
                         int sm_count, cudaStream_t stream);
 size_t bulk_smem_bytes(int tw, int stages);
+
+// Launch the fused ratio kernel (one warp per electron): ratio[e][0..4] =
+// sum_l {psi, dpsi/dx, dpsi/dy, dpsi/dz, lap psi}_l(r_e) cols[e][l]; also
+// writes p.values if it is not null.  p.grads/p.laps are ignored.
+cudaError_t launch_ratio(const EvalParams &p, int elem, const float *cols, float *ratio,
+                         int warps, cudaStream_t stream);
 
 // Optional spatial sort: writes perm[n_elec] (electron ids ordered by grid
 // brick).  scratch must hold sort_scratch_bytes(n_elec) bytes.

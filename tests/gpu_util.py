@@ -86,8 +86,15 @@ def compare(grid, lattice, coeffs, pos, gpu_out, storage=0, norm=0, scales=None,
             "max_bound_ratio": float(np.nanmax(ratio)),
         }
         bad = ~(ratio <= 1.0)
-        assert not bad.any(), (f"{name}: {int(bad.sum())} outputs break the bound; "
-                               f"worst ratio {float(np.nanmax(ratio)):.3g}")
+        if bad.any():
+            where = np.argwhere(bad)
+            rows = sorted(set(int(i) for i in where[:, 0]))
+            cols = sorted(set(int(i) for i in where[:, -1]))
+            raise AssertionError(
+                f"{name}: {int(bad.sum())} outputs break the bound; worst ratio "
+                f"{float(np.nanmax(ratio)):.3g}; electrons {rows[:12]} of {len(p)}, "
+                f"components {cols[:12]}; first bad: got {got[tuple(where[0])]!r} "
+                f"ref {ref[k][tuple(where[0])]!r}")
     return stats
 
 

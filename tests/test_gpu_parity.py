@@ -95,7 +95,7 @@ def test_kernel_configs_bitwise_identical(pb):
     pos = _edge_positions(lat, grid, rng)
     t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
     ref = gpu_eval(t, pos)
-    cfgs = [(v, c, w, s) for v in (1, 3) for c in (1, 2, 3) for w in (1, 4, 16) for s in (0, 1)]
+    cfgs = [(v, c, w, s) for v in (1, 3, 4) for c in (1, 2, 3) for w in (1, 4, 16) for s in (0, 1)]
     cfgs += [(2, tw, st, s) for tw in (1, 2, 4, 6, 8) for st in (2, 3, 8) for s in (0, 1)]
     for cfg in cfgs:
         t.set_kernel(*cfg)
@@ -114,7 +114,7 @@ def test_bulk_kernel_matches_register_kernel(pb, kind):
     pos = _edge_positions(lat, grid, np.random.default_rng(12))
     t = pb.BlipTable(grid, lat, tab, storage=pb.C64 if cplx else pb.BF16)
     ref = gpu_eval(t, pos)
-    for cfg in [(2, 1, 4, 0), (2, 3, 2, 1), (2, 8, 6, 0), (2, 5, 3, 0), (3, 1, 8, 0), (3, 1, 2, 1)]:
+    for cfg in [(2, 1, 4, 0), (2, 3, 2, 1), (2, 8, 6, 0), (2, 5, 3, 0), (3, 1, 8, 0), (3, 1, 2, 1), (4, 1, 4, 1)]:
         t.set_kernel(*cfg)
         for vo in (False, True):
             out = gpu_eval(t, pos, values_only=vo)

@@ -1,0 +1,125 @@
+"""Fused quasi-simultaneous ratio (blip_eval_ratio) against the FP64 oracle.
+
+For each walker, D[j][l] = psi_l(r_j) is built by the oracle at the current
+configuration and inverted in FP64; every electron then gets a Gaussian trial
+move r'_j, and the GPU returns sum_l {psi, grad psi, lap psi}_l(r'_j)
+(D^{-1})_{lj}.  Checks:
+  * against the oracle's outputs contracted in FP64, under the propagated
+    per-output bound plus the FP32 summation of the dot product;
+  * the matrix-determinant lemma: the value component equals
+    det(D with row j replaced by psi(r'_j)) / det(D);
+  * with no move (r'_j = r_j) the ratio is 1 (D D^{-1} = I);
+  * the optional new-row output equals blip_eval's values bitwise.
+"""
+import numpy as np
+import pytest
+
+import blip_inputs as bi
+import oracle
+import pins
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TAU32 = 8e-6
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1204_1121_gb300 as pb
+    return pb
+
+
+def _setup(n_orb=96, walkers=3, seed=5):
+    grid = (14, 12, 16)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, n_orb, seed=seed, sigma=2.0)
+    rng = np.random.default_rng(seed)
+    cur = [rng.uniform(0, 1, size=(n_orb, 3)) @ lat for _ in range(walkers)]
+    Dinv = []
+    for w in range(walkers):
+        v, _, _ = oracle.eval_stencil(grid, lat, tab, cur[w])
+        Dinv.append(np.linalg.inv(v))
+    return grid, lat, tab, cur, Dinv
+
+
+@pytest.mark.parametrize("storage,sort", [("f32", 0), ("f32", 1), ("bf16", 0)])
+def test_ratio_matches_oracle_and_determinant_lemma(pb, storage, sort):
+    grid, lat, tab, cur, Dinv = _setup()
+    n = tab.shape[-1]
+    rng = np.random.default_rng(17)
+    new = [c + rng.normal(0, 0.3, size=c.shape) for c in cur]
+    pos = np.concatenate(new)
+    offs = np.arange(0, len(pos) + 1, n, dtype=np.int32)
+    # electron j of walker w uses column j of that walker's inverse
+    cols = np.ascontiguousarray(np.concatenate([Di.T for Di in Dinv]), dtype=np.float32)  # [E][n]
+    kind = pb.F32 if storage == "f32" else pb.BF16
+    t = pb.BlipTable(grid, lat, tab, storage=kind)
+    dpos = torch.from_numpy(pos).cuda()
+    ratio, vals = t.eval_ratio(dpos, torch.from_numpy(cols).cuda(),
+                               torch.from_numpy(offs).cuda(), with_values=True, sort=sort)
+    torch.cuda.synchronize()
+    ratio = ratio.cpu().numpy().astype(np.float64)
+    rv, rg, rl, mag = oracle.eval_stencil(grid, lat, tab, pos, absmag=True)
+    c64 = cols.astype(np.float64)
+    ref = np.stack([(rv * c64).sum(1), (rg[:, 0] * c64).sum(1), (rg[:, 1] * c64).sum(1),
+                    (rg[:, 2] * c64).sum(1), (rl * c64).sum(1)], 1)
+    tau = TAU32 + (2.0 ** -8 if storage == "bf16" else 0.0)
+    outs = [rv, rg[:, 0], rg[:, 1], rg[:, 2], rl]
+    for k in range(5):
+        mk = mag[:, 0] if k == 0 else (mag[:, k] if k < 4 else mag[:, 4])
+        bound = (np.abs(c64) * tau * mk).sum(1) \
+            + 2 * (n / 32 + 8) * 2.0 ** -24 * (np.abs(outs[k] * c64)).sum(1) + 1e-12
+        assert (np.abs(ratio[:, k] - ref[:, k]) <= bound).all(), k
+    # matrix-determinant lemma on the value ratio, all in FP64: the new row
+    # dotted with column j of the FP64 inverse equals det(D_j') / det(D); the
+    # GPU value ratio then differs from it by the bound above plus the FP32
+    # rounding of the column (2^-24 sum |psi c|)
+    for w in range(len(cur)):
+        D, _, _ = oracle.eval_stencil(grid, lat, tab, cur[w])
+        d0 = np.linalg.slogdet(D)
+        newv, _, _ = oracle.eval_stencil(grid, lat, tab, new[w])
+        for j in (0, n // 2, n - 1):
+            Dj = D.copy()
+            Dj[j] = newv[j]
+            s1, l1 = np.linalg.slogdet(Dj)
+            lemma = s1 * d0[0] * np.exp(l1 - d0[1])
+            dot64 = float(newv[j] @ Dinv[w][:, j])
+            assert abs(dot64 - lemma) <= 1e-9 * (1 + abs(lemma)) * np.linalg.cond(D)
+            e = w * n + j
+            slack = 2.0 ** -24 * float(np.abs(newv[j] * Dinv[w][:, j]).sum())
+            assert abs(ratio[e, 0] - lemma) <= (np.abs(c64[e]) * tau * mag[e, 0]).sum() \
+                + 2 * (n / 32 + 8) * 2.0 ** -24 * float(np.abs(rv[e] * c64[e]).sum()) + slack + 1e-12
+    if storage == "f32":
+        ev, _, _ = t.eval(dpos)
+        assert np.array_equal(ev.cpu().numpy(), vals.cpu().numpy())
+    assert t.status() == 0
+
+
+def test_ratio_is_one_without_a_move(pb):
+    grid, lat, tab, cur, Dinv = _setup(n_orb=64, walkers=2, seed=8)
+    n = tab.shape[-1]
+    pos = np.concatenate(cur)
+    cols = np.ascontiguousarray(np.concatenate([Di.T for Di in Dinv]), dtype=np.float32)
+    t = pb.BlipTable(grid, lat, tab)
+    ratio, _ = t.eval_ratio(torch.from_numpy(pos).cuda(), torch.from_numpy(cols).cuda())
+    r = ratio.cpu().numpy().astype(np.float64)[:, 0]
+    rv, _, _, mag = oracle.eval_stencil(grid, lat, tab, pos, absmag=True)
+    c64 = cols.astype(np.float64)
+    # sum_l psi_l (D^{-1})_{lj} = 1; the FP32 column adds 2^-24 sum |psi c|, the
+    # GPU adds its per-output bound and the FP32 dot-product summation
+    s_abs = (np.abs(rv * c64)).sum(1)
+    bound = (np.abs(c64) * TAU32 * mag[:, 0]).sum(1) + (2 * (n / 32 + 8) + 1) * 2.0 ** -24 * s_abs
+    assert (np.abs(r - 1.0) <= bound + 1e-12).all()
+
+
+def test_ratio_rejects_complex_tables_and_bad_args(pb):
+    grid = (6, 6, 6)
+    tab = bi.smooth_random_table(grid, 4, seed=1, is_complex=True)
+    t = pb.BlipTable(grid, np.eye(3) * 6, tab, storage=pb.C64)
+    pos = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(pb.BlipError):
+        t.eval_ratio(pos, torch.zeros((3, 8), dtype=torch.float32, device="cuda"))
+    L = pb.lib()
+    assert L.blip_eval_ratio(None, None, 1, None, 0, None, None, None, 0, None) == -1
