@@ -123,7 +123,9 @@ int blip_create(const int grid[3], const double lattice[9], int n_orb, int stora
  *                    both non-NULL.
  *   stream           cudaStream_t
  * No host synchronisation and no allocation on the steady path (scratch for
- * the optional spatial sort is grown on the first call that needs it).
+ * the optional spatial sort is grown on the first call that needs it, after a
+ * device synchronisation).  The sort scratch belongs to the table: sorted
+ * evaluations of one table on different streams must not overlap in time.
  * Output buffers must not overlap each other or pos.  Errors: INVALID_ARG,
  * CUDA.  Device-side problems are reported through blip_status.
  */
@@ -167,14 +169,22 @@ int blip_info(blip_table t, long long out[8]);
 
 /*
  * blip_set_kernel - choose the evaluation kernel and its tile shape.
- *   variant    0: automatic (tuned choice); 1: register gather (each lane
- *              loads its orbitals' coefficients straight into registers);
- *              2: bulk-copy staging (one lane per warp streams the 4
- *              contiguous z-rows of each stencil column into shared memory
- *              with cp.async.bulk, other lanes consume them)
- *   chunks     orbital chunks of 32 lanes x (16 bytes / element size) that
- *              one warp evaluates per electron (1, 2, 3 or 6)
- *   warps      warps per block (1..16)
+ *   variant    0: automatic (tuned choice);
+ *              1: register gather (each lane loads its orbitals' coefficients
+ *                 straight into registers, 16 rows per batch);
+ *              2: bulk-copy staging (a producer warp streams the 4 contiguous
+ *                 z-rows of each stencil column into shared memory with
+ *                 cp.async.bulk; consumer warps contract them);
+ *              3: register gather, double-buffered batches (fully unrolled);
+ *              4: register gather, double-buffered batches (rolled loop);
+ *              5: cell-grouped register gather (electrons of one grid cell
+ *                 share every row load; always sorts)
+ *   chunks     variants 1, 3, 4: orbital chunks (32 lanes x 16 bytes) per
+ *              warp, 1..3 (1 for 16-bit storage); variant 2: consumer warps
+ *              per CTA, 1..8; variant 5: electrons per group, 2 or 4
+ *   warps      variants 1, 3, 4: warps per block, 1..16; variant 2:
+ *              shared-memory pipeline stages, 2..32; variant 5: warps per
+ *              block, 1..8
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2
  *              reuse for large batches)
  * Errors: INVALID_ARG for values outside those sets.
@@ -247,9 +257,10 @@ int blip_graph_destroy(blip_graph g);
  * Arguments, layouts, results and errors are those of blip_eval; the
  * evaluation kernel is the table's current choice (blip_set_kernel /
  * blip_autotune), always run on the cell-sorted order.
- * Limit: the scratch needed is about 4 (n1 n2 n3 + 1) + 8 n_elec bytes; a
- * batch that needs more than 8 MiB returns BLIP_ERR_SCRATCH_LIMIT and does
- * nothing (about 0.9 million electrons on the 72 x 72 x 48 grid).
+ * Limit: the scratch needed is about 4 (n1' n2' n3 + 1) + 8 n_elec bytes,
+ * with n1', n2' the grid sizes rounded up to multiples of 8; a batch that
+ * needs more than 8 MiB returns BLIP_ERR_SCRATCH_LIMIT and does nothing
+ * (about 0.9 million electrons on the 72 x 72 x 48 grid).
  * The table's device must be the current device.  The first call on a device
  * looks up the buffer's device address (which may load the library's code on
  * that device); make that first call before any stream capture.

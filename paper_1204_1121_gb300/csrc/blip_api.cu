@@ -166,7 +166,7 @@ int sorted_order(blip_table_s *t, const double *pos, int n_elec, cudaStream_t st
         CK(cudaStreamIsCapturing(stream, &cs));
         if (cs != cudaStreamCaptureStatusNone) return BLIP_ERR_INVALID_ARG;  // no growth in capture
         if (t->scratch) {
-            CK(cudaStreamSynchronize(t->last_stream));
+            CK(cudaDeviceSynchronize());   // earlier sorted evaluations may use it on any stream
             cudaFree(t->scratch);
         }
         t->scratch = nullptr;
@@ -188,13 +188,14 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
     p.row_stride = t->row_stride;
     p.Lreal = t->Lreal;
     p.nchunk = t->nchunk;
-    p.groups = (t->nchunk + kc.chunks - 1) / kc.chunks;
+    const bool grouped = kc.variant == VAR_GROUPED;
+    p.groups = grouped ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
     p.items = (long long)n_elec * p.groups;
     p.geo = t->geo;
     p.pos = pos;
     p.n_elec = n_elec;
     p.perm = nullptr;
-    if (kc.sort) {
+    if (kc.sort || grouped) {
         int *perm = nullptr;
         int rc = sorted_order(t, pos, n_elec, stream, &perm);
         if (rc) return rc;
@@ -212,6 +213,10 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
         int per_sm = (int)((228 * 1024) / (smem + 1024));
         per_sm = std::max(1, std::min(per_sm, 4));
         CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, stream));
+    } else if (grouped) {
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
+        CK(launch_grouped(p, t->elem, kc.chunks, kc.warps, keys, cell_end, stream));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
     }
@@ -489,6 +494,10 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
         if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
         if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
+    } else if (variant == VAR_GROUPED) {
+        // chunks = electrons per group (2 or 4); always evaluated in cell order
+        if ((chunks != 2 && chunks != 4) || warps < 1 || warps > 8) return BLIP_ERR_INVALID_ARG;
+        sort = 1;
     } else if (variant == VAR_BULK) {
         // chunks = consumer warps per CTA (chunks per tile), warps = pipeline stages
         if (chunks < 1 || chunks > 8 || warps < 2 || warps > 32) return BLIP_ERR_INVALID_ARG;
@@ -528,6 +537,9 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
             for (int st : {4, 8, 16})
                 if (bulk_smem_bytes(tw, st) <= 227 * 1024)
                     cands.push_back(KernelChoice{VAR_BULK, tw, st, srt});
+        if (srt)
+            for (int g : {2, 4})
+                for (int w : {4, 8}) cands.push_back(KernelChoice{VAR_GROUPED, g, w, 1});
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -729,7 +741,8 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
     p.row_stride = t->row_stride;
     p.Lreal = t->Lreal;
     p.nchunk = t->nchunk;
-    p.groups = (t->nchunk + kc.chunks - 1) / kc.chunks;
+    const bool grouped = kc.variant == VAR_GROUPED;
+    p.groups = grouped ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
     p.items = (long long)n_elec * p.groups;
     p.geo = t->geo;
     p.pos = pos;
@@ -748,6 +761,10 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
         int per_sm = (int)((228 * 1024) / (smem + 1024));
         per_sm = std::max(1, std::min(per_sm, 4));
         CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, s));
+    } else if (grouped) {
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, n_elec, scratch, &keys, &cell_end);
+        CK(launch_grouped(p, t->elem, kc.chunks, kc.warps, keys, cell_end, s));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, s));
     }

@@ -16,7 +16,8 @@ enum Variant {
     VAR_REGISTER = 1,         // batches of 16 rows, loads then contraction
     VAR_BULK = 2,             // bulk-copy producer/consumer pipeline
     VAR_REGISTER_PIPE = 3,    // double-buffered batches, fully unrolled
-    VAR_REGISTER_ROLLED = 4   // double-buffered batches, rolled loop
+    VAR_REGISTER_ROLLED = 4,  // double-buffered batches, rolled loop
+    VAR_GROUPED = 5           // electrons of one cell share each row load (sorted)
 };
 
 // Cell geometry, prepared once on the host in FP64.
@@ -78,6 +79,16 @@ cudaError_t launch_ratio(const EvalParams &p, int elem, const float *cols, float
 size_t sort_scratch_bytes(int n_elec, const Geometry &geo);
 cudaError_t launch_sort(const Geometry &geo, const double *pos, int n_elec, void *scratch,
                         int **perm_out, cudaStream_t stream);
+// After launch_sort: the electrons' cell keys and, per key, one past its last
+// slot in the sorted order.
+void sort_views(const Geometry &geo, int n_elec, void *scratch, const int **keys,
+                const int **cell_end);
+
+// Launch the cell-grouped kernel (needs the sort): warps whose slot leads a
+// group of up to `group` (2 or 4) electrons of the same cell evaluate them
+// together, reading each stencil row once for the whole group.
+cudaError_t launch_grouped(const EvalParams &p, int elem, int group, int warps, const int *keys,
+                           const int *cell_end, cudaStream_t stream);
 
 // Table construction kernels (blip_table.cu).
 // Convert rows [row0, row0 + nrows) of a source table [n1*n2*n3][Lreal]

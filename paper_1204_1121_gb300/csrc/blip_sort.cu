@@ -5,8 +5,16 @@
 // (Sec. IV.A, Eq. 11.12.23.1) into cache-friendly work; the paper itself
 // evaluates in input order.
 //
-// Counting sort over the n1*n2*n3 cells (plus one bucket for positions
-// without a cell), in four kernels:
+// The order is brick-major: the (a_1, a_2) plane is cut into 8 x 8 bricks of
+// whole z-columns, bricks in row-major order, and inside a brick the cells in
+// row-major order with z fastest (the table's own row order).  A window of
+// consecutively evaluated electrons then covers a compact 3-D region, so the
+// rows its stencils share along a_1 and a_2 are still in L2 when reused;
+// with a plain row-major cell order the a_1 neighbours come one whole
+// (a_2, a_3) plane later.
+//
+// Counting sort over these cell keys (plus one bucket for positions without
+// a cell), in four kernels:
 //   1. key of every electron (FP64 wrap, the same reduction as the
 //      evaluation) and a histogram of keys (atomicAdd),
 //   2-3. exclusive scan of the histogram (tile scans, then a scan of the tile
@@ -43,7 +51,10 @@ __global__ void sort_keys_kernel(Geometry geo, const double *__restrict__ pos, i
             if (i >= geo.n[a]) i -= geo.n[a];
             idx[a] = i;
         }
-        const int key = ok ? (idx[0] * geo.n[1] + idx[1]) * geo.n[2] + idx[2] : P;
+        const int nby = (geo.n[1] + 7) >> 3;
+        const int key = ok ? ((((idx[0] >> 3) * nby + (idx[1] >> 3)) * 8 + (idx[0] & 7)) * 8
+                              + (idx[1] & 7)) * geo.n[2] + idx[2]
+                           : P;
         keys[e] = key;
         atomicAdd(hist + key, 1);
     }
@@ -106,21 +117,41 @@ __global__ void sort_scatter_kernel(const int *__restrict__ keys, int n_elec,
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Cell keys: whole 8 x 8 bricks of z-columns, so the key range covers the
+// grid rounded up to multiples of 8 along a_1 and a_2.
+long long sort_buckets(const Geometry &geo)
+{
+    return (long long)((geo.n[0] + 7) / 8 * 8) * ((geo.n[1] + 7) / 8 * 8) * geo.n[2];
+}
+
 }  // namespace
 
 size_t sort_scratch_bytes(int n_elec, const Geometry &geo)
 {
-    const long long nb = (long long)geo.n[0] * geo.n[1] * geo.n[2] + 1;
+    const long long nb = sort_buckets(geo) + 1;
     const long long tiles = (nb + SCAN_TILE - 1) / SCAN_TILE;
     return align256(sizeof(int) * (size_t)nb) + 2 * align256(sizeof(int) * (size_t)n_elec)
          + 2 * align256(sizeof(int) * (size_t)(tiles + 1));
+}
+
+// Views into a sorted scratch: keys[e] of every electron and, after the
+// scatter, cell_end[k] = one past the last slot of key k (so key k occupies
+// slots [k ? cell_end[k - 1] : 0, cell_end[k])).
+void sort_views(const Geometry &geo, int n_elec, void *scratch, const int **keys,
+                const int **cell_end)
+{
+    const long long nb = sort_buckets(geo) + 1;
+    char *c = static_cast<char *>(scratch);
+    *cell_end = reinterpret_cast<const int *>(c);
+    *keys = reinterpret_cast<const int *>(c + align256(sizeof(int) * (size_t)nb));
+    (void)n_elec;
 }
 
 // Scratch layout: hist[P + 1] | keys[n_elec] | perm[n_elec] | sums | sums2.
 cudaError_t launch_sort(const Geometry &geo, const double *pos, int n_elec, void *scratch,
                         int **perm_out, cudaStream_t stream)
 {
-    const int P = geo.n[0] * geo.n[1] * geo.n[2];
+    const int P = (int)sort_buckets(geo);
     const int nb = P + 1;
     const int tiles = (nb + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles > SCAN_TILE) return cudaErrorInvalidValue;   // > 16.7M cells

@@ -96,6 +96,7 @@ def test_kernel_configs_bitwise_identical(pb):
     t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
     ref = gpu_eval(t, pos)
     cfgs = [(v, c, w, s) for v in (1, 3, 4) for c in (1, 2, 3) for w in (1, 4, 16) for s in (0, 1)]
+    cfgs += [(5, g, w, 1) for g in (2, 4) for w in (1, 4, 8)]
     cfgs += [(2, tw, st, s) for tw in (1, 2, 4, 6, 8) for st in (2, 3, 8) for s in (0, 1)]
     for cfg in cfgs:
         t.set_kernel(*cfg)
@@ -103,6 +104,41 @@ def test_kernel_configs_bitwise_identical(pb):
         for a, b in zip(ref, out):
             assert np.array_equal(a, b), cfg
     assert t.status() == 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_grouped_kernel_on_dense_cells(pb, storage):
+    """Many electrons per cell (groups of 1..4 plus remainders), duplicates and
+    cell-less positions: the cell-grouped kernel equals the register kernel
+    bitwise and the oracle within the bound."""
+    rng = np.random.default_rng(23)
+    grid = (6, 5, 7)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 300, seed=23)
+    n = np.array(grid, dtype=np.float64)
+    cells = rng.integers(0, 5, size=(12, 3))
+    counts = [1, 2, 3, 4, 5, 6, 7, 8, 9, 13, 17, 30]
+    u = np.concatenate([(c + rng.uniform(0.05, 0.95, size=(k, 3))) / n
+                        for c, k in zip(cells, counts)])
+    u = np.concatenate([u, u[:5], u[7:9] + 3.0])            # duplicates, far images
+    pos = u @ lat
+    pos = np.concatenate([pos[:40], [[np.nan, 0, 0], [0, np.inf, 1]], pos[40:]])
+    rng.shuffle(pos[42:])
+    kind = pb.F32 if storage == "f32" else pb.BF16
+    t = pb.BlipTable(grid, lat, tab, storage=kind)
+    t.set_kernel(1, 1, 8, 0)
+    ref = gpu_eval(t, pos)
+    t.status()
+    for cfg in [(5, 2, 4, 1), (5, 4, 8, 1), (5, 4, 1, 1), (5, 2, 8, 1)]:
+        t.set_kernel(*cfg)
+        for vo in (False, True):
+            out = gpu_eval(t, pos, values_only=vo)
+            for a, b in zip(ref, out):
+                assert np.array_equal(a, b, equal_nan=True), (cfg, vo)
+        assert t.status() & pb.STATUS_NONFINITE_POS
+    good = np.isfinite(pos).all(1)
+    compare(grid, lat, tab, pos[good], [r[good] for r in ref], storage=kind,
+            scales=_scales(tab, False))
 
 
 @pytest.mark.parametrize("kind", ["bf16", "c64"])
@@ -114,7 +150,8 @@ def test_bulk_kernel_matches_register_kernel(pb, kind):
     pos = _edge_positions(lat, grid, np.random.default_rng(12))
     t = pb.BlipTable(grid, lat, tab, storage=pb.C64 if cplx else pb.BF16)
     ref = gpu_eval(t, pos)
-    for cfg in [(2, 1, 4, 0), (2, 3, 2, 1), (2, 8, 6, 0), (2, 5, 3, 0), (3, 1, 8, 0), (3, 1, 2, 1), (4, 1, 4, 1)]:
+    for cfg in [(2, 1, 4, 0), (2, 3, 2, 1), (2, 8, 6, 0), (2, 5, 3, 0), (3, 1, 8, 0), (3, 1, 2, 1),
+                (4, 1, 4, 1), (5, 2, 4, 1), (5, 4, 8, 1)]:
         t.set_kernel(*cfg)
         for vo in (False, True):
             out = gpu_eval(t, pos, values_only=vo)
