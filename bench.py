@@ -36,6 +36,8 @@ import blip_inputs as bi  # noqa: E402
 # the kernel source it was measured on; reported as null once the kernel
 # changes.  Filled from the committed summary under profiles/.
 NCU_TRAFFIC = {
+    # (kernel source hash, workload, storage, electrons): (variant, chunks, bytes)
+    ("db994e9e1f6f1089", "tio2", "f32", 1536): (3, 2, 274803712 + 11272192),
 }
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "c64": 3, "bf16pair": 4}
@@ -53,6 +55,8 @@ def parse():
                              "tio2_super_complex"])
     ap.add_argument("--batch", type=int, default=1536, help="electrons per walker (tio2_batch)")
     ap.add_argument("--walkers", type=int, default=0, help="override walker count")
+    ap.add_argument("--orbitals", type=int, default=0,
+                    help="override the orbital count (smaller profiling cases)")
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--kernel", default="auto", help="auto | variant,chunks,warps,sort")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -68,6 +72,8 @@ def make_workload(args, rank):
         kw["batch"] = args.batch
     if args.walkers:
         kw["n_walkers"] = args.walkers
+    if args.orbitals:
+        kw["n_orb"] = args.orbitals
     w = bi.workload(args.workload, **kw)
     from paper_1204_1121_gb300 import replicas
     w.pos_seed = replicas.weak_seed(w.pos_seed, rank)   # each rank: its own walkers
@@ -327,6 +333,7 @@ def main():
     peak, peak_kind = measured_peaks()
     kh = kernel_hash()
     rec = NCU_TRAFFIC.get((kh, w.name, args.storage, E))
+    rec = rec[2] if rec and tuple(rec[:2]) == tuple(chosen[:2]) else None
     # FP32 FMA peak from unit counts and clock: SMs x 128 FP32 lanes x 2 FLOP
     # x 2.07 GHz (maximum SM clock)
     sms = info["sm_count"]
