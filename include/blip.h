@@ -202,6 +202,28 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
                   int chosen[4]);
 
 /*
+ * blip_set_kpoints - Bloch orbitals for a complex table.
+ *
+ * With k-points set, complex orbital l in [koffs[q], koffs[q + 1]) is
+ * psi_l(r) = exp(i k_q . r) u_l(r), where u_l is the periodic blip expansion
+ * held in the table (Eqs. 11.12.24.1 and 11.12.24.2) and
+ * k_q = 2 pi A^{-T} kappa_q.  blip_eval then returns psi, grad psi =
+ * e^{ik.r}(grad u + i k u) and lap psi = e^{ik.r}(lap u + 2 i k.grad u -
+ * |k|^2 u).  This lets a primitive-cell table with n_k k-points stand in for
+ * a supercell table n_k times larger (the paper's TiO2 orbitals are complex,
+ * Sec. VI.A; the phase convention is not stated there).
+ *   n_k      0 (clear) .. 16
+ *   kfrac    host [n_k][3] kappa_q in reciprocal-lattice units
+ *   koffs    host [n_k + 1] complex-orbital offsets, 0 = koffs[0] <= ... <=
+ *            koffs[n_k] = n_orb
+ * The phase uses the unwrapped fractional coordinates, reduced mod 1 in
+ * FP64.  Errors: INVALID_ARG, UNSUPPORTED_DTYPE (real tables).  The bulk-copy
+ * kernel (variant 2) has no Bloch epilogue and is not used while k-points
+ * are set.
+ */
+int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koffs);
+
+/*
  * blip_eval_ratio - fused quasi-simultaneous ratio (real orbitals).
  *
  * For the trial move r'_j of each electron (Sec. IV.A, Eq. 11.12.23.1) the

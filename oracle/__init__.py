@@ -14,6 +14,7 @@ Contents:
   Cartesian coordinates (tiny grids only).
 * ``kinetic`` - the Slater-only local kinetic energy built from orbital
   values and Laplacians (the energy-error probe of Sec. V.B).
+* ``bloch`` - k-point orbitals exp(i k.r) u(r) from a periodic table of u.
 
 Pins: every function here is checked in ``tests/test_oracle_pins.py`` against
 closed forms, invariants, exact polynomial and plane-wave reproduction, finite
@@ -135,4 +136,4 @@ def eval_stencil(grid, lattice, coeffs, pos, norm: int = 0, absmag: bool = False
     return (vals, grads, laps, mag) if absmag else (vals, grads, laps)
 
 
-from . import brute, kinetic  # noqa: E402,F401
+from . import bloch, brute, kinetic  # noqa: E402,F401

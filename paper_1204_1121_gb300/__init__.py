@@ -45,6 +45,7 @@ EXPORTED = {
     "blip_graph_destroy": (I, [P]),
     "blip_eval_sorted_noalloc": (I, [P, P, I, P, I, P, P, P, P]),
     "blip_eval_ratio": (I, [P, P, I, P, I, P, P, P, I, P]),
+    "blip_set_kpoints": (I, [P, I, P, P]),
 }
 
 _lock = threading.Lock()
@@ -253,6 +254,18 @@ class BlipTable:
         keys = ["rows", "row_stride", "Lreal", "elem_bytes", "table_bytes", "storage",
                 "sm_count", "variant"]
         return dict(zip(keys, [int(x) for x in a]))
+
+    def set_kpoints(self, kfrac, koffs):
+        """Bloch k-points (``blip_set_kpoints``): kfrac [n_k][3] in
+        reciprocal-lattice units, koffs [n_k + 1] complex-orbital offsets.
+        ``kfrac=None`` clears them."""
+        if kfrac is None:
+            _check(self._lib.blip_set_kpoints(self._h, 0, None, None), "blip_set_kpoints")
+            return
+        kf = np.ascontiguousarray(kfrac, dtype=np.float64).reshape(-1, 3)
+        ko = np.ascontiguousarray(koffs, dtype=np.int32)
+        _check(self._lib.blip_set_kpoints(self._h, kf.shape[0], P(kf.ctypes.data),
+                                          P(ko.ctypes.data)), "blip_set_kpoints")
 
     def set_kernel(self, variant=1, chunks=1, warps=8, sort=0):
         _check(self._lib.blip_set_kernel(self._h, variant, chunks, warps, sort), "blip_set_kernel")

@@ -53,6 +53,11 @@ struct blip_table_s {
     // spatial-sort scratch (grown outside stream capture)
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    // Bloch k-points (complex tables)
+    int n_k = 0;
+    int koff[kMaxKpoints + 1] = {};
+    double kfrac[kMaxKpoints][3] = {};
+    float kcart[kMaxKpoints][3] = {};
 };
 
 struct blip_graph_s {
@@ -129,6 +134,14 @@ int make_geometry(const int grid[3], const double lattice[9], int norm, Geometry
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+void copy_kpoints(const blip_table_s *t, EvalParams &p)
+{
+    p.n_k = t->n_k;
+    memcpy(p.koff, t->koff, sizeof(p.koff));
+    memcpy(p.kfrac, t->kfrac, sizeof(p.kfrac));
+    memcpy(p.kcart, t->kcart, sizeof(p.kcart));
+}
 
 int size_class(int n_elec)
 {
@@ -208,7 +221,9 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
     p.laps = static_cast<float *>(laps);
     p.vec_out = (t->Lreal % 4 == 0) && aligned16(values) && (!grads || (aligned16(grads) && aligned16(laps)));
     p.status = t->d_status;
+    copy_kpoints(t, p);
     if (kc.variant == VAR_BULK) {
+        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
         const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
         int per_sm = (int)((228 * 1024) / (smem + 1024));
         per_sm = std::max(1, std::min(per_sm, 4));
@@ -499,6 +514,7 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         if ((chunks != 2 && chunks != 4) || warps < 1 || warps > 8) return BLIP_ERR_INVALID_ARG;
         sort = 1;
     } else if (variant == VAR_BULK) {
+        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
         // chunks = consumer warps per CTA (chunks per tile), warps = pipeline stages
         if (chunks < 1 || chunks > 8 || warps < 2 || warps > 32) return BLIP_ERR_INVALID_ARG;
         if (bulk_smem_bytes(chunks, warps) > 227 * 1024) return BLIP_ERR_INVALID_ARG;
@@ -535,7 +551,7 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
             }
         for (int tw : tws)
             for (int st : {4, 8, 16})
-                if (bulk_smem_bytes(tw, st) <= 227 * 1024)
+                if (!t->n_k && bulk_smem_bytes(tw, st) <= 227 * 1024)
                     cands.push_back(KernelChoice{VAR_BULK, tw, st, srt});
         if (srt)
             for (int g : {2, 4})
@@ -574,6 +590,38 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
         chosen[2] = bestc.warps;
         chosen[3] = bestc.sort;
     }
+    return BLIP_OK;
+}
+
+int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koffs)
+{
+    if (!t) return BLIP_ERR_INVALID_ARG;
+    if (n_k == 0) {
+        t->n_k = 0;
+        return BLIP_OK;
+    }
+    if (!t->is_complex) return BLIP_ERR_UNSUPPORTED_DTYPE;
+    if (n_k < 0 || n_k > kMaxKpoints || !kfrac || !koffs) return BLIP_ERR_INVALID_ARG;
+    if (koffs[0] != 0 || koffs[n_k] != t->n_orb) return BLIP_ERR_INVALID_ARG;
+    for (int q = 0; q < n_k; ++q) {
+        if (koffs[q + 1] < koffs[q]) return BLIP_ERR_INVALID_ARG;
+        for (int c = 0; c < 3; ++c)
+            if (!isfinite(kfrac[3 * q + c])) return BLIP_ERR_INVALID_ARG;
+    }
+    // k_q = 2 pi A^{-T} kappa_q: component c = 2 pi sum_a kappa_a (A^{-1})_{a c}
+    const double two_pi = 6.283185307179586;
+    for (int q = 0; q < n_k; ++q)
+        for (int c = 0; c < 3; ++c) {
+            double k = 0.0;
+            for (int a = 0; a < 3; ++a) k += kfrac[3 * q + a] * t->geo.ainv[3 * a + c];
+            t->kcart[q][c] = (float)(two_pi * k);
+            t->kfrac[q][c] = kfrac[3 * q + c];
+        }
+    for (int q = 0; q <= n_k; ++q) t->koff[q] = koffs[q];
+    t->n_k = n_k;
+    if (t->choice.variant == VAR_BULK) t->choice = KernelChoice{VAR_REGISTER, 1, 8, 0};
+    for (auto &kv : t->tuned)
+        if (kv.second.variant == VAR_BULK) kv.second = KernelChoice{VAR_REGISTER, 1, 8, 0};
     return BLIP_OK;
 }
 
@@ -756,7 +804,9 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
     p.vec_out = (t->Lreal % 4 == 0) && aligned16(values) &&
                 (!grads || (aligned16(grads) && aligned16(laps)));
     p.status = t->d_status;
+    copy_kpoints(t, p);
     if (kc.variant == VAR_BULK) {
+        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
         const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
         int per_sm = (int)((228 * 1024) / (smem + 1024));
         per_sm = std::max(1, std::min(per_sm, 4));

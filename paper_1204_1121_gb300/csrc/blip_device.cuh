@@ -95,6 +95,7 @@ struct WarpSlice {
     float4 w4[64];
     float wl[64];
     int colrow[16];
+    float2 phase[kMaxKpoints];   // exp(2 pi i kappa_q . u) per k-point (Bloch tables)
 };
 
 // Combined weights of one electron: 64 x {value, grad x, grad y, grad z}
@@ -109,10 +110,11 @@ struct WarpWeights {
 // wrapped into [0, 1) (a tiny negative u that rounds up to 1 is the origin),
 // g = n_a u, i = floor(g) mod n_a, t = g - floor(g).  Returns status bits.
 __device__ __forceinline__ int wrap_axis(const Geometry &geo, int a, double rx, double ry,
-                                         double rz, int &i_out, float &t_out)
+                                         double rz, int &i_out, float &t_out, double *u_out = nullptr)
 {
     const double *ai = geo.ainv + 3 * a;
     const double u = fma(ai[0], rx, fma(ai[1], ry, ai[2] * rz));
+    if (u_out) *u_out = u;
     i_out = 0;
     t_out = 0.0f;
     if (!isfinite(u)) return BLIP_STATUS_NONFINITE_POS;
@@ -171,16 +173,31 @@ __device__ __forceinline__ int column_row(const Geometry &geo, int i0, int i1, i
 
 // Steps 1-2 for electron e: FP64 wrap on lanes 0-2, then weights and column
 // rows into the warp's slice.  Returns the warp-uniform status bits.
+template <bool BLOCH = false>
 __device__ __forceinline__ int stencil_setup_warp(const EvalParams &p, int e, int lane,
                                                   WarpSlice &ws)
 {
     int ia = 0, bad = 0;
     float ta = 0.0f;
+    double ua = 0.0;
     if (lane < 3) {
         const double *r = p.pos + 3 * (size_t)e;
-        bad = wrap_axis(p.geo, lane, r[0], r[1], r[2], ia, ta);
+        bad = wrap_axis(p.geo, lane, r[0], r[1], r[2], ia, ta, &ua);
     }
     bad = __reduce_or_sync(FULL, bad);
+    if constexpr (BLOCH) {
+        // Bloch phases from the unwrapped fractional coordinates (FP64
+        // reduction of kappa . u mod 1, then an FP32 sin/cos of 2 pi x)
+        const double u0 = __shfl_sync(FULL, ua, 0), u1 = __shfl_sync(FULL, ua, 1),
+                     u2 = __shfl_sync(FULL, ua, 2);
+        if (lane < p.n_k && !(bad & BLIP_STATUS_NONFINITE_POS)) {
+            const double *kf = p.kfrac[lane];
+            const double x = fma(kf[0], u0, fma(kf[1], u1, kf[2] * u2));
+            float sn, cs;
+            sincospif(2.0f * (float)(x - floor(x)), &sn, &cs);
+            ws.phase[lane] = make_float2(cs, sn);
+        }
+    }
     const int i0 = __shfl_sync(FULL, ia, 0), i1 = __shfl_sync(FULL, ia, 1),
               i2 = __shfl_sync(FULL, ia, 2);
     const float t0 = __shfl_sync(FULL, ta, 0), t1 = __shfl_sync(FULL, ta, 1),
@@ -198,9 +215,48 @@ __device__ __forceinline__ int stencil_setup_warp(const EvalParams &p, int e, in
 
 // Scale (quantised tables) and write the five outputs of one chunk
 // (32 lanes x VEC components) of electron e with streaming stores.
+// Bloch factor on the (re, im) pairs of one lane's components:
+// psi = ph u, grad psi = ph (grad u + i k u),
+// lap psi = ph (lap u + 2 i k . grad u - |k|^2 u).
 template <int VEC, bool VONLY>
-__device__ __forceinline__ void store_chunk(const EvalParams &p, int e, int chunk, int lane,
+__device__ __forceinline__ void apply_bloch(const EvalParams &p, int l0, const float2 *phase,
                                             float (&acc)[VONLY ? 1 : 5][VEC])
+{
+#pragma unroll
+    for (int v = 0; v < VEC; v += 2) {
+        const int lc = (l0 + v) >> 1;
+        int q = 0;
+        for (int j = 1; j < p.n_k; ++j) q += lc >= p.koff[j] ? 1 : 0;
+        const float2 ph = phase[q];
+        const float ur = acc[0][v], ui = acc[0][v + 1];
+        acc[0][v] = ph.x * ur - ph.y * ui;
+        acc[0][v + 1] = ph.x * ui + ph.y * ur;
+        if constexpr (!VONLY) {
+            const float k0 = p.kcart[q][0], k1 = p.kcart[q][1], k2 = p.kcart[q][2];
+            const float kk[3] = {k0, k1, k2};
+            float kgr = 0.0f, kgi = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float gr = acc[1 + c][v], gi = acc[1 + c][v + 1];
+                kgr = fmaf(kk[c], gr, kgr);
+                kgi = fmaf(kk[c], gi, kgi);
+                const float tr = gr - kk[c] * ui, ti = gi + kk[c] * ur;
+                acc[1 + c][v] = ph.x * tr - ph.y * ti;
+                acc[1 + c][v + 1] = ph.x * ti + ph.y * tr;
+            }
+            const float ksq = k0 * k0 + k1 * k1 + k2 * k2;
+            const float tr = acc[4][v] - 2.0f * kgi - ksq * ur;
+            const float ti = acc[4][v + 1] + 2.0f * kgr - ksq * ui;
+            acc[4][v] = ph.x * tr - ph.y * ti;
+            acc[4][v + 1] = ph.x * ti + ph.y * tr;
+        }
+    }
+}
+
+template <int VEC, bool VONLY, bool BLOCH = false>
+__device__ __forceinline__ void store_chunk(const EvalParams &p, int e, int chunk, int lane,
+                                            float (&acc)[VONLY ? 1 : 5][VEC],
+                                            const float2 *phase = nullptr)
 {
     constexpr int NW = VONLY ? 1 : 5;
     const size_t L = (size_t)p.Lreal;
@@ -217,6 +273,7 @@ __device__ __forceinline__ void store_chunk(const EvalParams &p, int e, int chun
             }
         }
     }
+    if constexpr (BLOCH) apply_bloch<VEC, VONLY>(p, l0, phase, acc);
     float *dst[5];
     dst[0] = p.values + (size_t)e * L + l0;
     if constexpr (!VONLY) {

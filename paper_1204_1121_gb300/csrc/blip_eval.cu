@@ -23,6 +23,8 @@
 //   4. scales (quantised tables) and writes the five outputs with streaming
 //      stores at the electron's original index.
 // No block-level synchronisation is needed: each warp owns its shared slice.
+#include <type_traits>
+
 #include "blip_device.cuh"
 
 namespace blip {
@@ -31,15 +33,16 @@ namespace {
 
 using namespace dev;
 
-template <int CPW, int VEC, bool VONLY>
+template <int CPW, int VEC, bool VONLY, bool BLOCH>
 __device__ __forceinline__ void store_outputs(const EvalParams &p, int e, int grp, int lane,
-                                              float (&acc)[CPW][VONLY ? 1 : 5][VEC])
+                                              float (&acc)[CPW][VONLY ? 1 : 5][VEC],
+                                              const WarpSlice &ws)
 {
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
         const int chunk = grp * CPW + c;
         if (chunk >= p.nchunk) break;                    // warp-uniform
-        store_chunk<VEC, VONLY>(p, e, chunk, lane, acc[c]);
+        store_chunk<VEC, VONLY, BLOCH>(p, e, chunk, lane, acc[c], ws.phase);
     }
 }
 
@@ -75,7 +78,7 @@ __device__ __forceinline__ void contract_rows(const WarpSlice &ws, int pt0,
 // Register-gather kernel: each lane loads its 16-byte slices of the 64 rows
 // straight into registers (4 columns = 16 rows in flight per batch for one
 // chunk, fewer for more chunks).
-template <typename T, int CPW, bool VONLY, int PIPE>
+template <typename T, int CPW, bool VONLY, int PIPE, bool BLOCH>
 __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 {
     constexpr int VEC = Elt<T>::VEC;
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                 for (int v = 0; v < VEC; ++v) acc[c][k][v] = 0.0f;
 
         __syncwarp();                      // previous item's readers are done with the slice
-        const int bad = stencil_setup_warp(p, e, lane, ws);
+        const int bad = stencil_setup_warp<BLOCH>(p, e, lane, ws);
         if (bad && lane == 0) atomicOr(p.status, bad);
         if (bad & BLIP_STATUS_NONFINITE_POS) {
 #pragma unroll
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                 for (int k = 0; k < NW; ++k)
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) acc[c][k][v] = __int_as_float(0x7fc00000);
-            store_outputs<CPW, VEC, VONLY>(p, e, grp, lane, acc);
+            store_outputs<CPW, VEC, VONLY, BLOCH>(p, e, grp, lane, acc, ws);
             continue;
         }
 
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                     }
             }
         }
-        store_outputs<CPW, VEC, VONLY>(p, e, grp, lane, acc);
+        store_outputs<CPW, VEC, VONLY, BLOCH>(p, e, grp, lane, acc, ws);
     }
 }
 
@@ -256,12 +259,20 @@ cudaError_t launch_register_t(const EvalParams &p, int warps, int pipe, cudaStre
     long long blocks = (p.items + warps - 1) / warps;
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    if (pipe == 2)
-        blip_eval_register<T, CPW, VONLY, 2><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
-    else if (pipe == 1)
-        blip_eval_register<T, CPW, VONLY, 1><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
-    else
-        blip_eval_register<T, CPW, VONLY, 0><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
+    const dim3 g((unsigned)blocks), b(32 * warps);
+    if (p.n_k) {
+        if constexpr (sizeof(T) == 2 && !std::is_same<T, __nv_bfloat16>::value) {
+            return cudaErrorInvalidValue;              // FP16 storage is real only
+        } else {
+            if (pipe == 2) blip_eval_register<T, CPW, VONLY, 2, true><<<g, b, smem, stream>>>(p);
+            else if (pipe == 1) blip_eval_register<T, CPW, VONLY, 1, true><<<g, b, smem, stream>>>(p);
+            else blip_eval_register<T, CPW, VONLY, 0, true><<<g, b, smem, stream>>>(p);
+        }
+    } else {
+        if (pipe == 2) blip_eval_register<T, CPW, VONLY, 2, false><<<g, b, smem, stream>>>(p);
+        else if (pipe == 1) blip_eval_register<T, CPW, VONLY, 1, false><<<g, b, smem, stream>>>(p);
+        else blip_eval_register<T, CPW, VONLY, 0, false><<<g, b, smem, stream>>>(p);
+    }
     return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@
 // group.  Warps whose slot is not a group leader return at once.  Each
 // output is still the same fixed-order 64-term sum as in the other kernels,
 // so results are bitwise identical to them.
+#include <type_traits>
+
 #include "blip_device.cuh"
 
 namespace blip {
@@ -15,7 +17,7 @@ namespace {
 
 using namespace dev;
 
-template <typename T, int G, bool VONLY>
+template <typename T, int G, bool VONLY, bool BLOCH>
 __global__ void __launch_bounds__(256) blip_eval_grouped(EvalParams p, const int *keys,
                                                          const int *cell_end)
 {
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(256) blip_eval_grouped(EvalParams p, const int
             if (m < gn) {
                 e[m] = p.perm[slot + m];
                 __syncwarp();
-                bad[m] = stencil_setup_warp(p, e[m], lane, ws[m]);
+                bad[m] = stencil_setup_warp<BLOCH>(p, e[m], lane, ws[m]);
                 if (bad[m] && lane == 0 && chunk == 0) atomicOr(p.status, bad[m]);
             }
         }
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(256) blip_eval_grouped(EvalParams p, const int
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) acc[m][k][v] = __int_as_float(0x7fc00000);
                 }
-                store_chunk<VEC, VONLY>(p, e[m], chunk, lane, acc[m]);
+                store_chunk<VEC, VONLY, BLOCH>(p, e[m], chunk, lane, acc[m], ws[m].phase);
             }
         }
     }
@@ -133,7 +135,17 @@ cudaError_t launch_grouped_t(const EvalParams &p, int warps, const int *keys, co
     long long blocks = (p.items + warps - 1) / warps;
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    blip_eval_grouped<T, G, VONLY><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p, keys, cell_end);
+    if (p.n_k) {
+        if constexpr (std::is_same<T, __half>::value) {
+            return cudaErrorInvalidValue;              // FP16 storage is real only
+        } else {
+            blip_eval_grouped<T, G, VONLY, true><<<(unsigned)blocks, 32 * warps, smem, stream>>>(
+                p, keys, cell_end);
+        }
+    } else {
+        blip_eval_grouped<T, G, VONLY, false><<<(unsigned)blocks, 32 * warps, smem, stream>>>(
+            p, keys, cell_end);
+    }
     return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@ enum Variant {
     VAR_GROUPED = 5           // electrons of one cell share each row load (sorted)
 };
 
+constexpr int kMaxKpoints = 16;
+
 // Cell geometry, prepared once on the host in FP64.
 struct Geometry {
     int n[3];          // grid points along a_1, a_2, a_3
@@ -50,6 +52,12 @@ struct EvalParams {
     float *laps;            // [n_elec][Lreal] or nullptr
     int vec_out;            // 1: outputs may be written with 16-byte stores
     int *status;            // device status word (atomicOr)
+    // Bloch phase (complex tables only): complex orbitals [koff[q], koff[q+1])
+    // carry exp(i k_q . r), k_q = 2 pi A^{-T} kappa_q; n_k = 0 for none.
+    int n_k;
+    int koff[kMaxKpoints + 1];
+    double kfrac[kMaxKpoints][3];
+    float kcart[kMaxKpoints][3];
 };
 
 // Stored elements per 16-byte vector.

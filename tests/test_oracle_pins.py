@@ -134,3 +134,76 @@ def test_local_kinetic_detects_swapped_index():
     assert T == pytest.approx(ref, rel=1e-10)
     Tt, _ = oracle.kinetic.local_kinetic(vals, laps.T, [(0, n)])
     assert abs(Tt - T) > 1e-6
+
+
+def _bloch_case():
+    rng = np.random.default_rng(31)
+    grid = (7, 6, 8)
+    lat = pins.triclinic_lattice()
+    tab = rng.normal(size=grid + (5,)) + 1j * rng.normal(size=grid + (5,))
+    kfrac = np.array([[0.0, 0.0, 0.0], [0.25, -0.5, 0.125], [0.5, 0.5, 0.5]])
+    koffs = [0, 1, 3, 5]
+    return grid, lat, tab, kfrac, koffs, rng
+
+
+def test_bloch_constant_u_is_a_plane_wave():
+    """u = c gives psi = c e^{ik.r}, grad = i k psi, lap = -|k|^2 psi."""
+    grid, lat, _, kfrac, koffs, rng = _bloch_case()
+    c = np.array([1.0 + 0.5j, -0.3 + 2j, 0.7 - 1j, 2.0 + 0j, -1j])
+    tab = np.broadcast_to(c, grid + (5,)).copy()
+    pos = rng.uniform(-5, 12, size=(30, 3))
+    v, g, lp = oracle.bloch.eval_bloch(grid, lat, tab, pos, kfrac, koffs)
+    kcart = 2 * np.pi * kfrac @ np.linalg.inv(lat.T)
+    for q in range(3):
+        for l in range(koffs[q], koffs[q + 1]):
+            k = kcart[q]
+            ref = c[l] * np.exp(1j * pos @ k)
+            assert np.abs(v[:, l] - ref).max() < 1e-12
+            assert np.abs(g[:, :, l] - 1j * k[None, :] * ref[:, None]).max() < 1e-11
+            assert np.abs(lp[:, l] + (k @ k) * ref).max() < 1e-10
+
+
+def test_bloch_theorem_translation():
+    """psi(r + R) = e^{ik.R} psi(r) for a lattice vector R."""
+    grid, lat, tab, kfrac, koffs, rng = _bloch_case()
+    pos = rng.uniform(0, 6, size=(20, 3))
+    R = 2 * lat[0] - lat[1] + 3 * lat[2]
+    a = oracle.bloch.eval_bloch(grid, lat, tab, pos, kfrac, koffs)
+    b = oracle.bloch.eval_bloch(grid, lat, tab, pos + R, kfrac, koffs)
+    kcart = 2 * np.pi * kfrac @ np.linalg.inv(lat.T)
+    for q in range(3):
+        f = np.exp(1j * kcart[q] @ R)
+        sl = slice(koffs[q], koffs[q + 1])
+        assert np.abs(b[0][:, sl] - f * a[0][:, sl]).max() < 1e-11
+        assert np.abs(b[1][:, :, sl] - f * a[1][:, :, sl]).max() < 1e-10
+        assert np.abs(b[2][:, sl] - f * a[2][:, sl]).max() < 1e-9
+
+
+def test_bloch_finite_differences():
+    grid, lat, tab, kfrac, koffs, rng = _bloch_case()
+    n = np.array(grid, dtype=np.float64)
+    g = rng.integers(0, 5, size=(12, 3)) + rng.uniform(0.2, 0.8, size=(12, 3))
+    pos = (g / n) @ lat
+    h = 1e-4
+    v0, g0, l0 = oracle.bloch.eval_bloch(grid, lat, tab, pos, kfrac, koffs)
+    fdg = np.zeros_like(g0)
+    fdl = np.zeros_like(l0)
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        vals = {s: oracle.bloch.eval_bloch(grid, lat, tab, pos + s * e, kfrac, koffs)
+                for s in (-2, -1, 1, 2)}
+        fdg[:, c] = (8 * (vals[1][0] - vals[-1][0]) - (vals[2][0] - vals[-2][0])) / (12 * h)
+        fdl += (8 * (vals[1][1][:, c] - vals[-1][1][:, c])
+                - (vals[2][1][:, c] - vals[-2][1][:, c])) / (12 * h)
+    assert np.abs(fdg - g0).max() / np.abs(g0).max() < 1e-7
+    assert np.abs(fdl - l0).max() / np.abs(l0).max() < 1e-6
+
+
+def test_bloch_gamma_point_is_the_plain_expansion():
+    grid, lat, tab, _, _, rng = _bloch_case()
+    pos = rng.uniform(-3, 9, size=(15, 3))
+    a = oracle.bloch.eval_bloch(grid, lat, tab, pos, [[0, 0, 0]], [0, 5])
+    b = oracle.eval_stencil(grid, lat, tab, pos)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
