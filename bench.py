@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tio2",
                     choices=["tio2", "tio2_batch", "tio2_precision", "cubic16",
-                             "tio2_super_complex"])
+                             "tio2_super_complex", "sm_update"])
     ap.add_argument("--batch", type=int, default=1536, help="electrons per walker (tio2_batch)")
     ap.add_argument("--walkers", type=int, default=0, help="override walker count")
     ap.add_argument("--orbitals", type=int, default=0,
@@ -243,8 +243,56 @@ def run_reference(args):
     return 0
 
 
+def run_sm(args):
+    """Sherman-Morrison inverse updates: 256 walkers x one accepted move each,
+    n = 768 (one spin of the 1,536-electron TiO2 cell).  HBM-bound: 12 n^2
+    bytes per walker update."""
+    import torch
+    import paper_1204_1121_gb300 as pb
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    W = args.walkers or 256
+    n = 768
+    g = torch.Generator(device="cuda").manual_seed(7)
+    dinv = torch.randn((W, n, n), generator=g, device="cuda") * 0.05
+    dinv += torch.eye(n, device="cuda")
+    rows = torch.randn((W, n), generator=g, device="cuda")
+    cols = torch.arange(W, dtype=torch.int32, device="cuda") % n
+    work = torch.empty((W, 2 * n), device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+    for k in range(max(3, args.warmup)):
+        pb.sm_update(dinv, rows, cols, work)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        pb.sm_update(dinv, rows, cols, work)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    bytes_alg = W * (12.0 * n * n + 16.0 * n)
+    peak, kind = measured_peaks()
+    ach = bytes_alg / (ms / 1e3) / 1e9
+    line = {"metric": "walker inverse updates/s (Sherman-Morrison, n=768)", "value": W / (ms / 1e3),
+            "unit": "updates/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"sm_update: {W} walkers x 1 accepted move, n = {n}",
+                       "l2": "flushed between steps (512 MB write)"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "traffic": None,
+                         "algorithmic_bytes_per_launch": bytes_alg},
+            "gpu_launches": 2 * args.steps}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "sm_update":
+        return run_sm(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch

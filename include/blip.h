@@ -248,6 +248,30 @@ int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walk
                     void *stream);
 
 /*
+ * blip_sm_update - Sherman-Morrison update of the inverse Slater matrices of
+ * a batch of walkers after one accepted move each (Sec. VI.D).
+ *
+ * Row j of walker w's matrix D_w (D[j][l] = psi_l(r_j)) is replaced by the
+ * new orbital row psi' (e.g. the `values` output of blip_eval_ratio).  With
+ * w_k = sum_l psi'_l Dinv[l][k] (w_j = xi, the acceptance ratio):
+ *     Dinv'[l][k] = Dinv[l][k] - Dinv[l][j] (w_k - delta_jk) / w_j.
+ *   n_walkers  >= 0 (<= 65535)
+ *   n          matrix order (electrons of one spin = orbitals), 1..32768
+ *   dinv       device [n_walkers][n][n] float, Dinv[l][k] row-major, updated
+ *              in place
+ *   rows       device [n_walkers][n] float: the new row of each walker
+ *   cols       device [n_walkers] int32: j, or -1 to leave the walker as is
+ *   work       device [n_walkers][2 n] float scratch, caller-owned
+ *   stream     cudaStream_t
+ * The move must have xi != 0 (a rejected or impossible move is not applied
+ * by the caller).  FP32 arithmetic; repeated updates accumulate rounding, so
+ * QMC codes recompute the inverse from scratch periodically.  Errors:
+ * INVALID_ARG, CUDA.
+ */
+int blip_sm_update(int n_walkers, int n, float *dinv, const float *rows, const int *cols,
+                   float *work, void *stream);
+
+/*
  * blip_graph_create - capture a fixed evaluation into a CUDA graph.
  * The graph evaluates pos[0 .. n_elec) with the given buffers in launches of
  * per_launch electrons each (per_launch = 1 reproduces one-at-a-time,

@@ -15,6 +15,7 @@ Contents:
 * ``kinetic`` - the Slater-only local kinetic energy built from orbital
   values and Laplacians (the energy-error probe of Sec. V.B).
 * ``bloch`` - k-point orbitals exp(i k.r) u(r) from a periodic table of u.
+* ``sherman_morrison`` - the O(N^2) inverse update after an accepted move.
 
 Pins: every function here is checked in ``tests/test_oracle_pins.py`` against
 closed forms, invariants, exact polynomial and plane-wave reproduction, finite
@@ -136,4 +137,4 @@ def eval_stencil(grid, lattice, coeffs, pos, norm: int = 0, absmag: bool = False
     return (vals, grads, laps, mag) if absmag else (vals, grads, laps)
 
 
-from . import bloch, brute, kinetic  # noqa: E402,F401
+from . import bloch, brute, kinetic, sherman_morrison  # noqa: E402,F401

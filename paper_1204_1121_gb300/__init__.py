@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["lib", "BlipTable", "BlipError", "F32", "BF16", "F16", "C64", "BF16PAIR",
+__all__ = ["lib", "BlipTable", "BlipError", "sm_update", "F32", "BF16", "F16", "C64", "BF16PAIR",
            "NORM_BSPLINE", "NORM_ALFE_GILLAN", "STATUS_NONFINITE_POS", "STATUS_FAR_POS",
            "STATUS_BAD_OFFSETS", "STATUS_TIMEOUT", "EXPORTED"]
 
@@ -46,6 +46,7 @@ EXPORTED = {
     "blip_eval_sorted_noalloc": (I, [P, P, I, P, I, P, P, P, P]),
     "blip_eval_ratio": (I, [P, P, I, P, I, P, P, P, I, P]),
     "blip_set_kpoints": (I, [P, I, P, P]),
+    "blip_sm_update": (I, [I, I, P, P, P, P, P]),
 }
 
 _lock = threading.Lock()
@@ -302,6 +303,24 @@ class BlipTable:
         if isinstance(x, torch.Tensor):
             return torch.view_as_complex(x.reshape(*x.shape[:-1], -1, 2))
         return x.view(np.complex64)
+
+
+def sm_update(dinv, rows, cols, work=None, stream=None):
+    """Sherman-Morrison row update of a batch of inverses (``blip_sm_update``).
+
+    dinv: CUDA float32 [W][n][n] (updated in place); rows: CUDA float32
+    [W][n]; cols: CUDA int32 [W] (-1 = no update).  Returns the work buffer
+    ([W][2n]: w = psi' Dinv, then the old column j)."""
+    import torch
+    W, n = dinv.shape[0], dinv.shape[1]
+    for x, dt in ((dinv, torch.float32), (rows, torch.float32), (cols, torch.int32)):
+        if not (x.is_cuda and x.dtype == dt and x.is_contiguous()):
+            raise TypeError("sm_update expects contiguous CUDA tensors (float32, float32, int32)")
+    if work is None:
+        work = torch.empty((W, 2 * n), dtype=torch.float32, device=dinv.device)
+    _check(lib().blip_sm_update(W, n, P(dinv.data_ptr()), P(rows.data_ptr()), P(cols.data_ptr()),
+                                P(work.data_ptr()), _stream_ptr(stream)), "blip_sm_update")
+    return work
 
 
 class BlipGraph:

@@ -593,6 +593,17 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     return BLIP_OK;
 }
 
+int blip_sm_update(int n_walkers, int n, float *dinv, const float *rows, const int *cols,
+                   float *work, void *stream)
+{
+    if (n_walkers < 0 || n < 1 || n > (1 << 15)) return BLIP_ERR_INVALID_ARG;
+    if (n_walkers == 0) return BLIP_OK;
+    if (!dinv || !rows || !cols || !work) return BLIP_ERR_INVALID_ARG;
+    if (n_walkers > 65535) return BLIP_ERR_INVALID_ARG;     // grid y/z limit
+    CK(launch_sm_update(n_walkers, n, dinv, rows, cols, work, static_cast<cudaStream_t>(stream)));
+    return BLIP_OK;
+}
+
 int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koffs)
 {
     if (!t) return BLIP_ERR_INVALID_ARG;

@@ -98,6 +98,11 @@ void sort_views(const Geometry &geo, int n_elec, void *scratch, const int **keys
 cudaError_t launch_grouped(const EvalParams &p, int elem, int group, int warps, const int *keys,
                            const int *cell_end, cudaStream_t stream);
 
+// Sherman-Morrison update of n_walkers inverses after one accepted move each
+// (blip_sm.cu); work holds [n_walkers][2 n] floats.
+cudaError_t launch_sm_update(int n_walkers, int n, float *dinv, const float *rows, const int *cols,
+                             float *work, cudaStream_t stream);
+
 // Table construction kernels (blip_table.cu).
 // Convert rows [row0, row0 + nrows) of a source table [n1*n2*n3][Lreal]
 // (src points at row row0) into the FP32 ghost-plane layout.

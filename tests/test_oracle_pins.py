@@ -207,3 +207,29 @@ def test_bloch_gamma_point_is_the_plain_expansion():
     b = oracle.eval_stencil(grid, lat, tab, pos)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_sherman_morrison_matches_direct_inverse():
+    rng = np.random.default_rng(51)
+    n = 40
+    D = rng.normal(size=(n, n)) + 4 * np.eye(n)
+    Dinv = np.linalg.inv(D)
+    for j in (0, 17, n - 1):
+        row = rng.normal(size=n)
+        new, w = oracle.sherman_morrison.sm_update(Dinv, row, j)
+        D2 = D.copy()
+        D2[j] = row
+        assert np.abs(new - np.linalg.inv(D2)).max() < 1e-10 * np.linalg.cond(D2)
+        assert np.abs(D2 @ new - np.eye(n)).max() < 1e-10 * np.linalg.cond(D2)
+        # w_j is the determinant ratio det(D') / det(D)
+        assert w[j] == pytest.approx(np.linalg.det(D2) / np.linalg.det(D), rel=1e-9)
+
+
+def test_sherman_morrison_unchanged_row_is_identity():
+    rng = np.random.default_rng(52)
+    n = 16
+    D = rng.normal(size=(n, n)) + 3 * np.eye(n)
+    Dinv = np.linalg.inv(D)
+    new, w = oracle.sherman_morrison.sm_update(Dinv, D[5], 5)
+    assert w[5] == pytest.approx(1.0, abs=1e-12)
+    assert np.abs(new - Dinv).max() < 1e-12 * np.abs(Dinv).max()
