@@ -434,7 +434,9 @@ def main():
         line["e2e"] = {"value": world * evals / (e_ms / 1e3), "unit": "orbital*electron evals/s",
                        "h2d_bytes_per_step": int(hp.numel() * 8 + ho.numel() * 4),
                        "d2h_bytes_per_step": int((hv.numel() + hg.numel() + hl.numel()) * 4),
-                       "ms_per_step": e_ms, "api": "blip_eval_host (pinned host buffers)"}
+                       "ms_per_step": e_ms,
+                       "api": "blip_eval_host with page-locked host buffers (the kernel reads the "
+                              "positions and writes the outputs across the host link)"}
 
     if not args.no_extra and args.workload == "tio2" and rank == 0:
         # one electron per launch (particle-by-particle order), 1,536 kernel

@@ -133,10 +133,13 @@ int blip_eval(blip_table t, const double *pos, int n_elec, const int *walker_off
               int n_walkers, void *values, void *grads, void *laps, void *stream);
 
 /*
- * blip_eval_host - blip_eval with HOST buffers: copies pos (and offsets) to
- * the device, evaluates, copies the outputs back, and synchronises.  Staging
- * buffers are owned by the table and grown as needed.  Same layouts and
- * errors as blip_eval; grads/laps may be NULL together.
+ * blip_eval_host - blip_eval with HOST buffers, synchronous.  If every buffer
+ * is page-locked (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory),
+ * the kernel reads the positions and writes the outputs through the host
+ * link directly, overlapping the transfers with the table gather; otherwise
+ * pos (and offsets) are copied to table-owned staging buffers (grown as
+ * needed), evaluated, and the outputs copied back.  Same layouts and errors
+ * as blip_eval; grads/laps may be NULL together.
  */
 int blip_eval_host(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
                    int n_walkers, void *values, void *grads, void *laps);
@@ -178,11 +181,14 @@ int blip_info(blip_table t, long long out[8]);
  *              3: register gather, double-buffered batches (fully unrolled);
  *              4: register gather, double-buffered batches (rolled loop);
  *              5: cell-grouped register gather (electrons of one grid cell
- *                 share every row load; always sorts)
- *   chunks     variants 1, 3, 4: orbital chunks (32 lanes x 16 bytes) per
+ *                 share every row load; always sorts);
+ *              6: as 3, with the warps of a block taking consecutive
+ *                 electrons of one chunk group and the row loads cached in
+ *                 L1 (shares rows between neighbours of a sorted batch)
+ *   chunks     variants 1, 3, 4, 6: orbital chunks (32 lanes x 16 bytes) per
  *              warp, 1..3 (1 for 16-bit storage); variant 2: consumer warps
  *              per CTA, 1..8; variant 5: electrons per group, 2 or 4
- *   warps      variants 1, 3, 4: warps per block, 1..16; variant 2:
+ *   warps      variants 1, 3, 4, 6: warps per block, 1..16; variant 2:
  *              shared-memory pipeline stages, 2..32; variant 5: warps per
  *              block, 1..8
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2

@@ -439,12 +439,42 @@ int blip_eval(blip_table t, const double *pos, int n_elec, const int *walker_off
                        static_cast<cudaStream_t>(stream), pick(t, n_elec));
 }
 
+// Device address of a pinned (page-locked) host buffer, or nullptr if p is
+// ordinary pageable memory.
+void *mapped_device_ptr(const void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int blip_eval_host(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
                    int n_walkers, void *values, void *grads, void *laps)
 {
     int rc = validate_eval(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps);
     if (rc) return rc;
     if (n_elec == 0) return BLIP_OK;
+    // Pinned host buffers: the kernel reads the positions and writes the
+    // outputs across the host link itself (zero-copy), so the transfers
+    // overlap the table gather instead of following it.
+    {
+        void *dp = mapped_device_ptr(pos), *dv = mapped_device_ptr(values);
+        void *dg = grads ? mapped_device_ptr(grads) : nullptr;
+        void *dl = laps ? mapped_device_ptr(laps) : nullptr;
+        void *doff = walker_offsets ? mapped_device_ptr(walker_offsets) : nullptr;
+        if (dp && dv && (!grads || (dg && dl)) && (!walker_offsets || doff)) {
+            rc = eval_device(t, static_cast<const double *>(dp), n_elec,
+                             static_cast<const int *>(doff), n_walkers, dv, dg, dl,
+                             t->own_stream, pick(t, n_elec));
+            if (rc) return rc;
+            CK(cudaStreamSynchronize(t->own_stream));
+            return BLIP_OK;
+        }
+    }
     const size_t L = (size_t)t->Lreal;
     const size_t pos_b = (size_t)n_elec * 3 * sizeof(double);
     const size_t off_b = walker_offsets ? (size_t)(n_walkers + 1) * sizeof(int) : 0;
@@ -505,7 +535,8 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         t->auto_mode = true;
         return BLIP_OK;
     }
-    if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE || variant == VAR_REGISTER_ROLLED) {
+    if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE || variant == VAR_REGISTER_ROLLED ||
+        variant == VAR_REGISTER_L1) {
         const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
         if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
         if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
@@ -548,6 +579,7 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
                 cands.push_back(KernelChoice{VAR_REGISTER, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_ROLLED, c, w, srt});
+                if (srt) cands.push_back(KernelChoice{VAR_REGISTER_L1, c, w, srt});
             }
         for (int tw : tws)
             for (int st : {4, 8, 16})

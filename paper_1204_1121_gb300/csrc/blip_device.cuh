@@ -53,6 +53,17 @@ __device__ __forceinline__ uint4 ldg_stream(const void *p)
     return r;
 }
 
+// 16-byte read-only load that allocates in L1: used when the warps of one
+// block read the same stencil rows (consecutive electrons of a sorted batch).
+__device__ __forceinline__ uint4 ldg_shared_rows(const void *p)
+{
+    uint4 r;
+    asm("ld.global.nc.L1::evict_last.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
+    return r;
+}
+
 template <typename T> struct Elt;
 template <> struct Elt<float> {
     static constexpr int VEC = 4;
@@ -173,9 +184,14 @@ __device__ __forceinline__ int column_row(const Geometry &geo, int i0, int i1, i
 
 // Steps 1-2 for electron e: FP64 wrap on lanes 0-2, then weights and column
 // rows into the warp's slice.  Returns the warp-uniform status bits.
+// Geometry half of the per-electron setup: FP64 wrap on lanes 0-2, the 16
+// stencil-column rows into the warp's slice (and the Bloch phases), then a
+// __syncwarp.  Returns the warp-uniform status bits; t0..t2 receive the
+// FP32 offsets for stencil_weights_warp.
 template <bool BLOCH = false>
-__device__ __forceinline__ int stencil_setup_warp(const EvalParams &p, int e, int lane,
-                                                  WarpSlice &ws)
+__device__ __forceinline__ int stencil_geometry_warp(const EvalParams &p, int e, int lane,
+                                                     WarpSlice &ws, float &t0, float &t1,
+                                                     float &t2)
 {
     int ia = 0, bad = 0;
     float ta = 0.0f;
@@ -200,16 +216,37 @@ __device__ __forceinline__ int stencil_setup_warp(const EvalParams &p, int e, in
     }
     const int i0 = __shfl_sync(FULL, ia, 0), i1 = __shfl_sync(FULL, ia, 1),
               i2 = __shfl_sync(FULL, ia, 2);
-    const float t0 = __shfl_sync(FULL, ta, 0), t1 = __shfl_sync(FULL, ta, 1),
-                t2 = __shfl_sync(FULL, ta, 2);
+    t0 = __shfl_sync(FULL, ta, 0);
+    t1 = __shfl_sync(FULL, ta, 1);
+    t2 = __shfl_sync(FULL, ta, 2);
     if (bad & BLIP_STATUS_NONFINITE_POS) return bad;
+    if (lane < 16) ws.colrow[lane] = column_row(p.geo, i0, i1, i2, lane);
+    __syncwarp();
+    return bad;
+}
+
+// Weights half: the 64 x 5 combined weights into the warp's slice (two
+// sites per lane), then a __syncwarp.
+__device__ __forceinline__ void stencil_weights_warp(const EvalParams &p, float t0, float t1,
+                                                     float t2, int lane, WarpSlice &ws)
+{
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int pt = lane + 32 * h;
         site_weights(p.geo, t0, t1, t2, pt, ws.w4[pt], ws.wl[pt]);
     }
-    if (lane < 16) ws.colrow[lane] = column_row(p.geo, i0, i1, i2, lane);
     __syncwarp();
+}
+
+// Both halves: everything a warp needs before contracting electron e.
+template <bool BLOCH = false>
+__device__ __forceinline__ int stencil_setup_warp(const EvalParams &p, int e, int lane,
+                                                  WarpSlice &ws)
+{
+    float t0, t1, t2;
+    const int bad = stencil_geometry_warp<BLOCH>(p, e, lane, ws, t0, t1, t2);
+    if (bad & BLIP_STATUS_NONFINITE_POS) return bad;
+    stencil_weights_warp(p, t0, t1, t2, lane, ws);
     return bad;
 }
 

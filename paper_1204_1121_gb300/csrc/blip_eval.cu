@@ -75,6 +75,13 @@ __device__ __forceinline__ void contract_rows(const WarpSlice &ws, int pt0,
     }
 }
 
+template <bool L1ALLOC>
+__device__ __forceinline__ uint4 load_row(const void *p)
+{
+    if constexpr (L1ALLOC) return ldg_shared_rows(p);
+    else return ldg_stream(p);
+}
+
 // Register-gather kernel: each lane loads its 16-byte slices of the 64 rows
 // straight into registers (4 columns = 16 rows in flight per batch for one
 // chunk, fewer for more chunks).
@@ -95,10 +102,23 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
     const char *tbase = reinterpret_cast<const char *>(p.table);
     const size_t rowb = (size_t)p.row_stride * sizeof(T);
 
-    for (long long item = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); item < p.items;
+    // PIPE == 3: the warps of a block take consecutive electrons for the same
+    // chunk group, so in a sorted batch they share stencil rows through L1
+    const long long total = PIPE == 3
+        ? (long long)((p.n_elec + wpb - 1) / wpb) * p.groups * wpb : p.items;
+    for (long long item = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); item < total;
          item += nwarps) {
-        const int slot = (int)(item / p.groups);
-        const int grp = (int)(item - (long long)slot * p.groups);
+        int slot, grp;
+        if constexpr (PIPE == 3) {
+            const long long blk = item / wpb;
+            const long long eb = blk / p.groups;
+            grp = (int)(blk - eb * p.groups);
+            slot = (int)(eb * wpb + (item - blk * wpb));
+            if (slot >= p.n_elec) continue;                 // warp-uniform
+        } else {
+            slot = (int)(item / p.groups);
+            grp = (int)(item - (long long)slot * p.groups);
+        }
         const int e = p.perm ? p.perm[slot] : slot;
 
         float acc[CPW][NW][VEC];
@@ -110,7 +130,10 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                 for (int v = 0; v < VEC; ++v) acc[c][k][v] = 0.0f;
 
         __syncwarp();                      // previous item's readers are done with the slice
-        const int bad = stencil_setup_warp<BLOCH>(p, e, lane, ws);
+        float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+        constexpr bool EARLY = PIPE == 1 || PIPE == 3;   // first loads before the weights
+        const int bad = EARLY ? stencil_geometry_warp<BLOCH>(p, e, lane, ws, t0, t1, t2)
+                              : stencil_setup_warp<BLOCH>(p, e, lane, ws);
         if (bad && lane == 0) atomicOr(p.status, bad);
         if (bad & BLIP_STATUS_NONFINITE_POS) {
 #pragma unroll
@@ -164,7 +187,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                 }
                 contract_rows<T, CPW, VEC, VONLY, RB>(ws, (b + 1) * RB, b1, acc);
             }
-        } else if constexpr (PIPE == 1) {
+        } else if constexpr (PIPE == 1 || PIPE == 3) {
             // software-pipelined: the next batch of RB rows is in flight while
             // the current batch is contracted (two register buffers)
             constexpr int RB = CPW == 1 ? 8 : (CPW == 2 ? 4 : 2);
@@ -174,8 +197,9 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
             for (int r = 0; r < RB; ++r) {
                 const char *rp = tbase + (size_t)(ws.colrow[r >> 2] + (r & 3)) * rowb;
 #pragma unroll
-                for (int c = 0; c < CPW; ++c) buf[0][r][c] = ldg_stream(rp + coff[c]);
+                for (int c = 0; c < CPW; ++c) buf[0][r][c] = load_row<PIPE == 3>(rp + coff[c]);
             }
+            stencil_weights_warp(p, t0, t1, t2, lane, ws);   // overlaps the first loads
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 if (b + 1 < NB) {
@@ -185,7 +209,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                         const char *rp = tbase + (size_t)(ws.colrow[pt >> 2] + (pt & 3)) * rowb;
 #pragma unroll
                         for (int c = 0; c < CPW; ++c)
-                            buf[(b + 1) & 1][r][c] = ldg_stream(rp + coff[c]);
+                            buf[(b + 1) & 1][r][c] = load_row<PIPE == 3>(rp + coff[c]);
                     }
                 }
 #pragma unroll
@@ -259,17 +283,23 @@ cudaError_t launch_register_t(const EvalParams &p, int warps, int pipe, cudaStre
     long long blocks = (p.items + warps - 1) / warps;
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+    if (pipe == 3) {                 // whole blocks of consecutive electrons per chunk group
+        blocks = (long long)((p.n_elec + warps - 1) / warps) * p.groups;
+        if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+    }
     const dim3 g((unsigned)blocks), b(32 * warps);
     if (p.n_k) {
         if constexpr (sizeof(T) == 2 && !std::is_same<T, __nv_bfloat16>::value) {
             return cudaErrorInvalidValue;              // FP16 storage is real only
         } else {
-            if (pipe == 2) blip_eval_register<T, CPW, VONLY, 2, true><<<g, b, smem, stream>>>(p);
+            if (pipe == 3) blip_eval_register<T, CPW, VONLY, 3, true><<<g, b, smem, stream>>>(p);
+            else if (pipe == 2) blip_eval_register<T, CPW, VONLY, 2, true><<<g, b, smem, stream>>>(p);
             else if (pipe == 1) blip_eval_register<T, CPW, VONLY, 1, true><<<g, b, smem, stream>>>(p);
             else blip_eval_register<T, CPW, VONLY, 0, true><<<g, b, smem, stream>>>(p);
         }
     } else {
-        if (pipe == 2) blip_eval_register<T, CPW, VONLY, 2, false><<<g, b, smem, stream>>>(p);
+        if (pipe == 3) blip_eval_register<T, CPW, VONLY, 3, false><<<g, b, smem, stream>>>(p);
+        else if (pipe == 2) blip_eval_register<T, CPW, VONLY, 2, false><<<g, b, smem, stream>>>(p);
         else if (pipe == 1) blip_eval_register<T, CPW, VONLY, 1, false><<<g, b, smem, stream>>>(p);
         else blip_eval_register<T, CPW, VONLY, 0, false><<<g, b, smem, stream>>>(p);
     }
@@ -307,9 +337,11 @@ cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, 
                         cudaStream_t stream)
 {
     if (warps < 1 || warps > 16) return cudaErrorInvalidValue;
-    if (variant != VAR_REGISTER && variant != VAR_REGISTER_PIPE && variant != VAR_REGISTER_ROLLED)
+    if (variant != VAR_REGISTER && variant != VAR_REGISTER_PIPE && variant != VAR_REGISTER_ROLLED &&
+        variant != VAR_REGISTER_L1)
         return cudaErrorInvalidValue;
-    const int pipe = variant == VAR_REGISTER_PIPE ? 1 : (variant == VAR_REGISTER_ROLLED ? 2 : 0);
+    const int pipe = variant == VAR_REGISTER_PIPE ? 1
+                   : variant == VAR_REGISTER_ROLLED ? 2 : variant == VAR_REGISTER_L1 ? 3 : 0;
     switch (elem) {
     case ELEM_F32: return launch_register<float>(p, chunks, warps, pipe, stream);
     case ELEM_BF16: return launch_register<__nv_bfloat16>(p, chunks, warps, pipe, stream);

@@ -21,35 +21,41 @@ constexpr int SM_THREADS = 256;
 constexpr int SM_ROWS = 8;      // rows of Dinv per thread in the rank-1 pass
 
 // w[wk][k] = sum_l rows[wk][l] Dinv[wk][l][k]; colj[wk][l] = Dinv[wk][l][j].
-__global__ void __launch_bounds__(SM_THREADS) sm_gemv_kernel(int n, const float *__restrict__ dinv,
-                                                             const float *__restrict__ rows,
-                                                             const int *__restrict__ cols,
-                                                             float *__restrict__ work)
+// A block covers 32 columns (one coalesced 128-byte segment per row) and
+// splits the rows over SM_PARTS warps; the partial sums meet in shared
+// memory in a fixed order.
+constexpr int SM_PARTS = 8;
+
+__global__ void __launch_bounds__(32 * SM_PARTS) sm_gemv_kernel(int n, const float *__restrict__ dinv,
+                                                                const float *__restrict__ rows,
+                                                                const int *__restrict__ cols,
+                                                                float *__restrict__ work)
 {
-    __shared__ float srow[SM_THREADS];
+    __shared__ float part[SM_PARTS][32];
     const int wk = blockIdx.y;
     const int j = cols[wk];
     if (j < 0 || j >= n) return;                       // no accepted move for this walker
     const float *D = dinv + (size_t)wk * n * n;
     const float *r = rows + (size_t)wk * n;
     float *w = work + (size_t)wk * 2 * n;
-    const int k = blockIdx.x * SM_THREADS + threadIdx.x;
+    const int lane = threadIdx.x & 31, pw = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
     float acc = 0.0f;
-    for (int l0 = 0; l0 < n; l0 += SM_THREADS) {
-        const int m = min(SM_THREADS, n - l0);
-        __syncthreads();
-        if (threadIdx.x < m) srow[threadIdx.x] = r[l0 + threadIdx.x];
-        __syncthreads();
-        if (k < n) {
-            const float *Dl = D + (size_t)l0 * n + k;
-#pragma unroll 8
-            for (int i = 0; i < m; ++i) acc = fmaf(srow[i], Dl[(size_t)i * n], acc);
-        }
-    }
     if (k < n) {
-        w[k] = acc;
-        w[n + k] = D[(size_t)k * n + j];                  // column j, kept before the update
+        const int l0 = (int)((long long)n * pw / SM_PARTS), l1 = (int)((long long)n * (pw + 1) / SM_PARTS);
+#pragma unroll 8
+        for (int l = l0; l < l1; ++l) acc = fmaf(__ldg(r + l), D[(size_t)l * n + k], acc);
     }
+    part[pw][lane] = acc;
+    __syncthreads();
+    if (pw == 0 && k < n) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < SM_PARTS; ++q) s += part[q][lane];
+        w[k] = s;
+    }
+    // column j, kept before the update: rows k of this block's range, by warp 1
+    if (pw == 1 && k < n) w[n + k] = D[(size_t)k * n + j];
 }
 
 // Dinv[l][k] -= colj[l] (w_k - delta_jk) / w_j.
@@ -79,8 +85,8 @@ __global__ void __launch_bounds__(SM_THREADS) sm_rank1_kernel(int n, float *__re
 cudaError_t launch_sm_update(int n_walkers, int n, float *dinv, const float *rows, const int *cols,
                              float *work, cudaStream_t stream)
 {
-    const dim3 g1((n + SM_THREADS - 1) / SM_THREADS, n_walkers);
-    sm_gemv_kernel<<<g1, SM_THREADS, 0, stream>>>(n, dinv, rows, cols, work);
+    const dim3 g1((n + 31) / 32, n_walkers);
+    sm_gemv_kernel<<<g1, 32 * SM_PARTS, 0, stream>>>(n, dinv, rows, cols, work);
     const dim3 g2((n + SM_THREADS - 1) / SM_THREADS, (n + SM_ROWS - 1) / SM_ROWS, n_walkers);
     sm_rank1_kernel<<<g2, SM_THREADS, 0, stream>>>(n, dinv, cols, work);
     return cudaGetLastError();
