@@ -278,6 +278,18 @@ int blip_sm_update(int n_walkers, int n, float *dinv, const float *rows, const i
                    float *work, void *stream);
 
 /*
+ * blip_test_stall_pipeline - test hook for the failure path (no counterpart
+ * in the paper).  With on != 0, launches of the bulk-copy kernel (variant 2)
+ * on this table stall their own pipeline: the consumer warps never release
+ * the first stage, so the producer's bounded wait runs out, it drains the
+ * copies it has in flight, and the consumers' bounded waits run out too.
+ * The launch returns after a few seconds with BLIP_STATUS_TIMEOUT set and
+ * undefined outputs; the context stays usable.  on = 0 restores normal
+ * operation.  Nothing faults, traps or spins without a bound.
+ */
+int blip_test_stall_pipeline(blip_table t, int on);
+
+/*
  * blip_graph_create - capture a fixed evaluation into a CUDA graph.
  * The graph evaluates pos[0 .. n_elec) with the given buffers in launches of
  * per_launch electrons each (per_launch = 1 reproduces one-at-a-time,

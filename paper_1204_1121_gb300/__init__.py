@@ -47,6 +47,7 @@ EXPORTED = {
     "blip_eval_ratio": (I, [P, P, I, P, I, P, P, P, I, P]),
     "blip_set_kpoints": (I, [P, I, P, P]),
     "blip_sm_update": (I, [I, I, P, P, P, P, P]),
+    "blip_test_stall_pipeline": (I, [P, I]),
 }
 
 _lock = threading.Lock()

@@ -53,6 +53,8 @@ struct blip_table_s {
     // spatial-sort scratch (grown outside stream capture)
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    // test hook: stall the bulk kernel's pipeline (bounded waits run out)
+    int test_stall = 0;
     // Bloch k-points (complex tables)
     int n_k = 0;
     int koff[kMaxKpoints + 1] = {};
@@ -227,7 +229,8 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
         const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
         int per_sm = (int)((228 * 1024) / (smem + 1024));
         per_sm = std::max(1, std::min(per_sm, 4));
-        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, stream));
+        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, t->test_stall,
+                       stream));
     } else if (grouped) {
         const int *keys = nullptr, *cell_end = nullptr;
         sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
@@ -625,6 +628,13 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     return BLIP_OK;
 }
 
+int blip_test_stall_pipeline(blip_table t, int on)
+{
+    if (!t) return BLIP_ERR_INVALID_ARG;
+    t->test_stall = on ? 1 : 0;
+    return BLIP_OK;
+}
+
 int blip_sm_update(int n_walkers, int n, float *dinv, const float *rows, const int *cols,
                    float *work, void *stream)
 {
@@ -853,7 +863,7 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
         const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
         int per_sm = (int)((228 * 1024) / (smem + 1024));
         per_sm = std::max(1, std::min(per_sm, 4));
-        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, s));
+        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, t->test_stall, s));
     } else if (grouped) {
         const int *keys = nullptr, *cell_end = nullptr;
         sort_views(t->geo, n_elec, scratch, &keys, &cell_end);

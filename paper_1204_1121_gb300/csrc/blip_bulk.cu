@@ -108,6 +108,7 @@ struct BulkArgs {
     int ntiles;      // tiles per row
     int stages;      // ring depth S
     int stage_bytes; // 4 rows x tw x 512 bytes
+    int stall;       // test hook: consumers never release the first stage
 };
 
 template <typename T, bool VONLY>
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(288) blip_eval_bulk(EvalParams p, BulkArgs b)
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(empty + s);
+            if (lane == 0 && !(b.stall && k == 0)) mbar_arrive(empty + s);
             ++k;
         }
         if (bad && lane == 0 && cw == 0 && tile == 0) atomicOr(p.status, bad);
@@ -286,9 +287,10 @@ __global__ void __launch_bounds__(288) blip_eval_bulk(EvalParams p, BulkArgs b)
 
 template <typename T, bool VONLY>
 cudaError_t launch_bulk_t(const EvalParams &p, int tw, int stages, int ctas_per_sm, int sm_count,
-                          cudaStream_t stream)
+                          int stall, cudaStream_t stream)
 {
     BulkArgs b;
+    b.stall = stall;
     b.tw = tw;
     b.ntiles = (p.nchunk + tw - 1) / tw;
     b.stages = stages;
@@ -314,10 +316,10 @@ cudaError_t launch_bulk_t(const EvalParams &p, int tw, int stages, int ctas_per_
 
 template <typename T>
 cudaError_t launch_bulk_elem(const EvalParams &p, int tw, int stages, int ctas_per_sm,
-                             int sm_count, cudaStream_t stream)
+                             int sm_count, int stall, cudaStream_t stream)
 {
-    if (p.grads) return launch_bulk_t<T, false>(p, tw, stages, ctas_per_sm, sm_count, stream);
-    return launch_bulk_t<T, true>(p, tw, stages, ctas_per_sm, sm_count, stream);
+    if (p.grads) return launch_bulk_t<T, false>(p, tw, stages, ctas_per_sm, sm_count, stall, stream);
+    return launch_bulk_t<T, true>(p, tw, stages, ctas_per_sm, sm_count, stall, stream);
 }
 
 }  // namespace
@@ -329,14 +331,16 @@ size_t bulk_smem_bytes(int tw, int stages)
 }
 
 cudaError_t launch_bulk(const EvalParams &p, int elem, int tw, int stages, int ctas_per_sm,
-                        int sm_count, cudaStream_t stream)
+                        int sm_count, int stall, cudaStream_t stream)
 {
     if (tw < 1 || tw > 8 || stages < 2 || stages > 64 || ctas_per_sm < 1) return cudaErrorInvalidValue;
     switch (elem) {
-    case ELEM_F32: return launch_bulk_elem<float>(p, tw, stages, ctas_per_sm, sm_count, stream);
+    case ELEM_F32:
+        return launch_bulk_elem<float>(p, tw, stages, ctas_per_sm, sm_count, stall, stream);
     case ELEM_BF16:
-        return launch_bulk_elem<__nv_bfloat16>(p, tw, stages, ctas_per_sm, sm_count, stream);
-    case ELEM_F16: return launch_bulk_elem<__half>(p, tw, stages, ctas_per_sm, sm_count, stream);
+        return launch_bulk_elem<__nv_bfloat16>(p, tw, stages, ctas_per_sm, sm_count, stall, stream);
+    case ELEM_F16:
+        return launch_bulk_elem<__half>(p, tw, stages, ctas_per_sm, sm_count, stall, stream);
     default: return cudaErrorInvalidValue;
     }
 }

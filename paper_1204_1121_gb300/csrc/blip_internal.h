@@ -74,8 +74,10 @@ cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, 
 
 // Launch the bulk-copy kernel: tw chunks per tile (consumer warps, 1..8),
 // `stages` shared-memory stages, ctas_per_sm persistent CTAs per SM.
+// stall != 0 is a test hook: the consumers never release the first stage, so
+// the bounded waits run out and BLIP_STATUS_TIMEOUT is raised.
 cudaError_t launch_bulk(const EvalParams &p, int elem, int tw, int stages, int ctas_per_sm,
-                        int sm_count, cudaStream_t stream);
+                        int sm_count, int stall, cudaStream_t stream);
 size_t bulk_smem_bytes(int tw, int stages);
 
 // Launch the fused ratio kernel (one warp per electron): ratio[e][0..4] =

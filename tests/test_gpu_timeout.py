@@ -1,0 +1,45 @@
+"""The bounded waits of the bulk-copy kernel: a stalled pipeline (test hook,
+the consumers never release the first stage) makes the waits run out after
+about two seconds; the kernel returns, reports BLIP_STATUS_TIMEOUT, and the
+same context evaluates correctly afterwards.  No fault, trap or unbounded
+spin is involved."""
+import time
+
+import numpy as np
+import pytest
+
+import blip_inputs as bi
+import pins
+from gpu_util import compare, gpu_eval
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1204_1121_gb300 as pb
+    return pb
+
+
+def test_stalled_pipeline_times_out_and_context_survives(pb):
+    grid = (8, 8, 8)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 128, seed=61)
+    pos = np.random.default_rng(61).uniform(0, 1, size=(64, 3)) @ lat
+    t = pb.BlipTable(grid, lat, tab)
+    t.set_kernel(2, 1, 2, 0)                 # bulk copy, 2 stages
+    t.status()
+    pb.lib().blip_test_stall_pipeline(t.handle, 1)
+    t0 = time.time()
+    gpu_eval(t, pos)
+    dt = time.time() - t0
+    st = t.status()
+    assert st & pb.STATUS_TIMEOUT
+    assert 1.0 < dt < 30.0
+    pb.lib().blip_test_stall_pipeline(t.handle, 0)
+    out = gpu_eval(t, pos)
+    assert t.status() == 0
+    compare(grid, lat, tab, pos, out)
