@@ -173,9 +173,14 @@ int validate_eval(const blip_table_s *t, const double *pos, int n_elec, const in
 
 // Spatial sort of the batch into the table's scratch (grown outside stream
 // capture); *perm receives the evaluation order.
-int sorted_order(blip_table_s *t, const double *pos, int n_elec, cudaStream_t stream, int **perm)
+int sorted_order(blip_table_s *t, const double *pos, int n_elec, cudaStream_t stream, int **perm,
+                 const ElecGeo **georec = nullptr)
 {
-    const size_t need = sort_scratch_bytes(n_elec, t->geo);
+    // sort scratch, then (optionally) per-electron geometry records by
+    // electron and by slot
+    const size_t sort_b = (sort_scratch_bytes(n_elec, t->geo) + 255) & ~(size_t)255;
+    const size_t rec_b = sizeof(ElecGeo) * (size_t)n_elec;
+    const size_t need = sort_b + (georec ? 2 * rec_b : 0);
     if (t->scratch_bytes < need) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         CK(cudaStreamIsCapturing(stream, &cs));
@@ -189,7 +194,14 @@ int sorted_order(blip_table_s *t, const double *pos, int n_elec, cudaStream_t st
         CK(cudaMalloc(&t->scratch, need));
         t->scratch_bytes = need;
     }
-    CK(launch_sort(t->geo, pos, n_elec, t->scratch, perm, stream));
+    if (georec) {
+        ElecGeo *by_e = reinterpret_cast<ElecGeo *>(static_cast<char *>(t->scratch) + sort_b);
+        ElecGeo *by_slot = by_e + n_elec;
+        CK(launch_sort(t->geo, pos, n_elec, t->scratch, perm, stream, by_e, by_slot));
+        *georec = by_slot;
+    } else {
+        CK(launch_sort(t->geo, pos, n_elec, t->scratch, perm, stream));
+    }
     return BLIP_OK;
 }
 
@@ -212,9 +224,12 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
     p.perm = nullptr;
     if (kc.sort || grouped) {
         int *perm = nullptr;
-        int rc = sorted_order(t, pos, n_elec, stream, &perm);
+        const ElecGeo *rec = nullptr;
+        const bool want_rec = t->n_k == 0 && kc.variant != VAR_BULK;
+        int rc = sorted_order(t, pos, n_elec, stream, &perm, want_rec ? &rec : nullptr);
         if (rc) return rc;
         p.perm = perm;
+        p.georec = rec;
     }
     p.offsets = offs;
     p.n_walkers = offs ? n_walkers : 0;
@@ -702,9 +717,11 @@ int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walk
     p.perm = nullptr;
     if (sort) {
         int *perm = nullptr;
-        int rc = sorted_order(t, pos, n_elec, s, &perm);
+        const ElecGeo *rec = nullptr;
+        int rc = sorted_order(t, pos, n_elec, s, &perm, &rec);
         if (rc) return rc;
         p.perm = perm;
+        p.georec = rec;
     }
     p.offsets = walker_offsets;
     p.n_walkers = walker_offsets ? n_walkers : 0;

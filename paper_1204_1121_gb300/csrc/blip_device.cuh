@@ -188,11 +188,26 @@ __device__ __forceinline__ int column_row(const Geometry &geo, int i0, int i1, i
 // stencil-column rows into the warp's slice (and the Bloch phases), then a
 // __syncwarp.  Returns the warp-uniform status bits; t0..t2 receive the
 // FP32 offsets for stencil_weights_warp.
-template <bool BLOCH = false>
+// GEO: 0 = FP64 wrap here, 1 = FP64 wrap + Bloch phases, 2 = read the
+// per-slot record the sort pre-pass made (its FP64 wrap already done).
+template <int GEO = 0>
 __device__ __forceinline__ int stencil_geometry_warp(const EvalParams &p, int e, int lane,
                                                      WarpSlice &ws, float &t0, float &t1,
-                                                     float &t2)
+                                                     float &t2, int slot = -1)
 {
+    constexpr bool BLOCH = GEO == 1;
+    if constexpr (GEO == 2) {
+        // geometry already reduced in FP64 by the sort pre-pass
+        const int4 gi = *reinterpret_cast<const int4 *>(p.georec + slot);
+        const float4 gt = *reinterpret_cast<const float4 *>(&p.georec[slot].t[0]);
+        t0 = gt.x;
+        t1 = gt.y;
+        t2 = gt.z;
+        if (gi.w & BLIP_STATUS_NONFINITE_POS) return gi.w;
+        if (lane < 16) ws.colrow[lane] = column_row(p.geo, gi.x, gi.y, gi.z, lane);
+        __syncwarp();
+        return gi.w;
+    } else {
     int ia = 0, bad = 0;
     float ta = 0.0f;
     double ua = 0.0;
@@ -223,6 +238,7 @@ __device__ __forceinline__ int stencil_geometry_warp(const EvalParams &p, int e,
     if (lane < 16) ws.colrow[lane] = column_row(p.geo, i0, i1, i2, lane);
     __syncwarp();
     return bad;
+    }
 }
 
 // Weights half: the 64 x 5 combined weights into the warp's slice (two
@@ -239,12 +255,12 @@ __device__ __forceinline__ void stencil_weights_warp(const EvalParams &p, float 
 }
 
 // Both halves: everything a warp needs before contracting electron e.
-template <bool BLOCH = false>
+template <int GEO = 0>
 __device__ __forceinline__ int stencil_setup_warp(const EvalParams &p, int e, int lane,
-                                                  WarpSlice &ws)
+                                                  WarpSlice &ws, int slot = -1)
 {
     float t0, t1, t2;
-    const int bad = stencil_geometry_warp<BLOCH>(p, e, lane, ws, t0, t1, t2);
+    const int bad = stencil_geometry_warp<GEO>(p, e, lane, ws, t0, t1, t2, slot);
     if (bad & BLIP_STATUS_NONFINITE_POS) return bad;
     stencil_weights_warp(p, t0, t1, t2, lane, ws);
     return bad;

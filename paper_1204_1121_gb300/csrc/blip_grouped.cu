@@ -17,7 +17,7 @@ namespace {
 
 using namespace dev;
 
-template <typename T, int G, bool VONLY, bool BLOCH>
+template <typename T, int G, bool VONLY, int GEO>
 __global__ void __launch_bounds__(256) blip_eval_grouped(EvalParams p, const int *keys,
                                                          const int *cell_end)
 {
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) blip_eval_grouped(EvalParams p, const int
             if (m < gn) {
                 e[m] = p.perm[slot + m];
                 __syncwarp();
-                bad[m] = stencil_setup_warp<BLOCH>(p, e[m], lane, ws[m]);
+                bad[m] = stencil_setup_warp<GEO>(p, e[m], lane, ws[m], slot + m);
                 if (bad[m] && lane == 0 && chunk == 0) atomicOr(p.status, bad[m]);
             }
         }
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) blip_eval_grouped(EvalParams p, const int
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) acc[m][k][v] = __int_as_float(0x7fc00000);
                 }
-                store_chunk<VEC, VONLY, BLOCH>(p, e[m], chunk, lane, acc[m], ws[m].phase);
+                store_chunk<VEC, VONLY, GEO == 1>(p, e[m], chunk, lane, acc[m], ws[m].phase);
             }
         }
     }
@@ -139,11 +139,14 @@ cudaError_t launch_grouped_t(const EvalParams &p, int warps, const int *keys, co
         if constexpr (std::is_same<T, __half>::value) {
             return cudaErrorInvalidValue;              // FP16 storage is real only
         } else {
-            blip_eval_grouped<T, G, VONLY, true><<<(unsigned)blocks, 32 * warps, smem, stream>>>(
+            blip_eval_grouped<T, G, VONLY, 1><<<(unsigned)blocks, 32 * warps, smem, stream>>>(
                 p, keys, cell_end);
         }
+    } else if (p.georec) {
+        blip_eval_grouped<T, G, VONLY, 2><<<(unsigned)blocks, 32 * warps, smem, stream>>>(
+            p, keys, cell_end);
     } else {
-        blip_eval_grouped<T, G, VONLY, false><<<(unsigned)blocks, 32 * warps, smem, stream>>>(
+        blip_eval_grouped<T, G, VONLY, 0><<<(unsigned)blocks, 32 * warps, smem, stream>>>(
             p, keys, cell_end);
     }
     return cudaGetLastError();

@@ -33,6 +33,15 @@ struct Geometry {
     float norm;        // 1, or (3/2)^3 for phi(0) = 1 blips
 };
 
+// Per-electron geometry computed once by the sort pre-pass (FP64 wrap done
+// there): base cell, FP32 offsets and status bits, stored in slot order.
+struct __align__(16) ElecGeo {
+    int i[3];
+    int bad;
+    float t[3];
+    float pad;
+};
+
 // Everything one evaluation launch needs (passed by value as the kernel
 // parameter).
 struct EvalParams {
@@ -47,6 +56,7 @@ struct EvalParams {
     const double *pos;      // [n_elec][3]
     int n_elec;
     const int *perm;        // evaluation order of the electrons, or nullptr
+    const ElecGeo *georec;  // per-slot geometry from the sort pre-pass, or nullptr
     const int *offsets;     // [n_walkers + 1] or nullptr
     int n_walkers;
     float *values;          // [n_elec][Lreal]
@@ -72,6 +82,13 @@ inline int elem_bytes(int elem) { return elem == ELEM_F32 ? 4 : 2; }
 cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, int warps,
                         cudaStream_t stream);
 
+// Register-gather instantiations (blip_reg_*.cu): pipe 0..3 as the variants.
+cudaError_t launch_register_f32_c1(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
+cudaError_t launch_register_f32_c2(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
+cudaError_t launch_register_f32_c3(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
+cudaError_t launch_register_bf16(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
+cudaError_t launch_register_f16(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
+
 // Launch the bulk-copy kernel: tw chunks per tile (consumer warps, 1..8),
 // `stages` shared-memory stages, ctas_per_sm persistent CTAs per SM.
 // stall != 0 is a test hook: the consumers never release the first stage, so
@@ -90,7 +107,8 @@ cudaError_t launch_ratio(const EvalParams &p, int elem, const float *cols, float
 // brick).  scratch must hold sort_scratch_bytes(n_elec) bytes.
 size_t sort_scratch_bytes(int n_elec, const Geometry &geo);
 cudaError_t launch_sort(const Geometry &geo, const double *pos, int n_elec, void *scratch,
-                        int **perm_out, cudaStream_t stream);
+                        int **perm_out, cudaStream_t stream, ElecGeo *rec_by_e = nullptr,
+                        ElecGeo *rec_by_slot = nullptr);
 // After launch_sort: the electrons' cell keys and, per key, one past its last
 // slot in the sorted order.
 void sort_views(const Geometry &geo, int n_elec, void *scratch, const int **keys,

@@ -27,7 +27,7 @@ namespace {
 
 using namespace dev;
 
-template <typename T>
+template <typename T, int GEO>
 __global__ void __launch_bounds__(256) blip_eval_ratio_kernel(EvalParams p, const float *cols,
                                                               float *ratio)
 {
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) blip_eval_ratio_kernel(EvalParams p, cons
          slot += nwarps) {
         const int e = p.perm ? p.perm[slot] : (int)slot;
         __syncwarp();
-        const int bad = stencil_setup_warp(p, e, lane, ws);
+        const int bad = stencil_setup_warp<GEO>(p, e, lane, ws, (int)slot);
         if (bad && lane == 0) atomicOr(p.status, bad);
         float dot[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (bad & BLIP_STATUS_NONFINITE_POS) {
@@ -129,7 +129,10 @@ cudaError_t launch_ratio_t(const EvalParams &p, const float *cols, float *ratio,
     long long blocks = ((long long)p.n_elec + warps - 1) / warps;
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    blip_eval_ratio_kernel<T><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p, cols, ratio);
+    if (p.georec)
+        blip_eval_ratio_kernel<T, 2><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p, cols, ratio);
+    else
+        blip_eval_ratio_kernel<T, 0><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p, cols, ratio);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@
 // The order inside one cell is not deterministic, but every electron's result
 // is computed independently, so the outputs are.
 #include "blip_internal.h"
+#include "../../include/blip.h"
 
 namespace blip {
 
@@ -33,23 +34,41 @@ constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __global__ void sort_keys_kernel(Geometry geo, const double *__restrict__ pos, int n_elec,
-                                 int *__restrict__ keys, int *__restrict__ hist, int P)
+                                 int *__restrict__ keys, int *__restrict__ hist, int P,
+                                 ElecGeo *__restrict__ rec)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_elec; e += gridDim.x * blockDim.x) {
         const double rx = pos[3 * (size_t)e], ry = pos[3 * (size_t)e + 1],
                      rz = pos[3 * (size_t)e + 2];
         int idx[3];
+        float tt[3];
+        int badbits = 0;
         bool ok = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
+            // the same FP64 reduction as the evaluation kernels' wrap
             const double u = fma(geo.ainv[3 * a], rx, fma(geo.ainv[3 * a + 1], ry,
                                                           geo.ainv[3 * a + 2] * rz));
+            tt[a] = 0.0f;
             if (!isfinite(u)) { ok = false; idx[a] = 0; continue; }
+            if (fabs(u) > 1099511627776.0) badbits |= BLIP_STATUS_FAR_POS;   // 2^40
             double w = u - floor(u);
             if (w >= 1.0) w = 0.0;
-            int i = (int)floor((double)geo.n[a] * w);
+            const double g = (double)geo.n[a] * w;
+            const double fi = floor(g);
+            tt[a] = (float)(g - fi);
+            int i = (int)fi;
             if (i >= geo.n[a]) i -= geo.n[a];
             idx[a] = i;
+        }
+        if (!ok) badbits |= BLIP_STATUS_NONFINITE_POS;
+        if (rec) {
+            ElecGeo r;
+            r.i[0] = idx[0]; r.i[1] = idx[1]; r.i[2] = idx[2];
+            r.bad = badbits;
+            r.t[0] = tt[0]; r.t[1] = tt[1]; r.t[2] = tt[2];
+            r.pad = 0.0f;
+            rec[e] = r;
         }
         const int nby = (geo.n[1] + 7) >> 3;
         const int key = ok ? ((((idx[0] >> 3) * nby + (idx[1] >> 3)) * 8 + (idx[0] & 7)) * 8
@@ -109,10 +128,15 @@ __global__ void add_tile_offsets_kernel(int *__restrict__ data, int n, const int
 }
 
 __global__ void sort_scatter_kernel(const int *__restrict__ keys, int n_elec,
-                                    int *__restrict__ cursor, int *__restrict__ perm)
+                                    int *__restrict__ cursor, int *__restrict__ perm,
+                                    const ElecGeo *__restrict__ rec,
+                                    ElecGeo *__restrict__ rec_sorted)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_elec; e += gridDim.x * blockDim.x)
-        perm[atomicAdd(cursor + keys[e], 1)] = e;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_elec; e += gridDim.x * blockDim.x) {
+        const int slot = atomicAdd(cursor + keys[e], 1);
+        perm[slot] = e;
+        if (rec_sorted) rec_sorted[slot] = rec[e];
+    }
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -149,8 +173,10 @@ void sort_views(const Geometry &geo, int n_elec, void *scratch, const int **keys
 
 // Scratch layout: hist[P + 1] | keys[n_elec] | perm[n_elec] | sums | sums2.
 cudaError_t launch_sort(const Geometry &geo, const double *pos, int n_elec, void *scratch,
-                        int **perm_out, cudaStream_t stream)
+                        int **perm_out, cudaStream_t stream, ElecGeo *rec_by_e,
+                        ElecGeo *rec_by_slot)
 {
+    if ((rec_by_e == nullptr) != (rec_by_slot == nullptr)) return cudaErrorInvalidValue;
     const int P = (int)sort_buckets(geo);
     const int nb = P + 1;
     const int tiles = (nb + SCAN_TILE - 1) / SCAN_TILE;
@@ -170,12 +196,12 @@ cudaError_t launch_sort(const Geometry &geo, const double *pos, int n_elec, void
     if (e != cudaSuccess) return e;
     const int eb = (n_elec + 255) / 256;
     sort_keys_kernel<<<eb < 1 ? 1 : (eb > 65535 * 8 ? 65535 * 8 : eb), 256, 0, stream>>>(
-        geo, pos, n_elec, keys, hist, P);
+        geo, pos, n_elec, keys, hist, P, rec_by_e);
     scan_tiles_kernel<<<tiles, SCAN_THREADS, 0, stream>>>(hist, nb, sums);
     scan_tiles_kernel<<<1, SCAN_THREADS, 0, stream>>>(sums, tiles, sums2);
     add_tile_offsets_kernel<<<(nb + 255) / 256, 256, 0, stream>>>(hist, nb, sums);
     sort_scatter_kernel<<<eb < 1 ? 1 : (eb > 65535 * 8 ? 65535 * 8 : eb), 256, 0, stream>>>(
-        keys, n_elec, hist, perm);
+        keys, n_elec, hist, perm, rec_by_e, rec_by_slot);
     *perm_out = perm;
     return cudaGetLastError();
 }
