@@ -184,11 +184,13 @@ int blip_info(blip_table t, long long out[8]);
  *                 share every row load; always sorts);
  *              6: as 3, with the warps of a block taking consecutive
  *                 electrons of one chunk group and the row loads cached in
- *                 L1 (shares rows between neighbours of a sorted batch)
- *   chunks     variants 1, 3, 4, 6: orbital chunks (32 lanes x 16 bytes) per
+ *                 L1 (shares rows between neighbours of a sorted batch);
+ *              7: as 6, the warps of a block stepping through the row
+ *                 batches in lockstep (one block barrier per batch)
+ *   chunks     variants 1, 3, 4, 6, 7: orbital chunks (32 lanes x 16 bytes) per
  *              warp, 1..3 (1 for 16-bit storage); variant 2: consumer warps
  *              per CTA, 1..8; variant 5: electrons per group, 2 or 4
- *   warps      variants 1, 3, 4, 6: warps per block, 1..16; variant 2:
+ *   warps      variants 1, 3, 4, 6, 7: warps per block, 1..16; variant 2:
  *              shared-memory pipeline stages, 2..32; variant 5: warps per
  *              block, 1..8
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2

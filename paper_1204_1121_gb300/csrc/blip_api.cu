@@ -554,7 +554,7 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         return BLIP_OK;
     }
     if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE || variant == VAR_REGISTER_ROLLED ||
-        variant == VAR_REGISTER_L1) {
+        variant == VAR_REGISTER_L1 || variant == VAR_REGISTER_LOCKSTEP) {
         const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
         if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
         if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
@@ -598,6 +598,7 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
                 cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_ROLLED, c, w, srt});
                 if (srt) cands.push_back(KernelChoice{VAR_REGISTER_L1, c, w, srt});
+                if (srt) cands.push_back(KernelChoice{VAR_REGISTER_LOCKSTEP, c, w, srt});
             }
         for (int tw : tws)
             for (int st : {4, 8, 16})

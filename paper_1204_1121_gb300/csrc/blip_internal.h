@@ -18,8 +18,9 @@ enum Variant {
     VAR_REGISTER_PIPE = 3,    // double-buffered batches, fully unrolled
     VAR_REGISTER_ROLLED = 4,  // double-buffered batches, rolled loop
     VAR_GROUPED = 5,          // electrons of one cell share each row load (sorted)
-    VAR_REGISTER_L1 = 6       // double-buffered; a block's warps take consecutive
+    VAR_REGISTER_L1 = 6,      // double-buffered; a block's warps take consecutive
                               // electrons of one chunk group and share rows via L1
+    VAR_REGISTER_LOCKSTEP = 7 // as 6, the block's warps in lockstep per row batch
 };
 
 constexpr int kMaxKpoints = 16;

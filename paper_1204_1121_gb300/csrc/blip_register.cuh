@@ -108,17 +108,26 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 
     // PIPE == 3: the warps of a block take consecutive electrons for the same
     // chunk group, so in a sorted batch they share stencil rows through L1
-    const long long total = PIPE == 3
+    // PIPE == 4: as 3, and the warps of a block step through the row batches
+    // in lockstep (a block barrier per batch), so a row one warp brings into
+    // L1 is still there when its neighbours ask for it
+    constexpr bool BLOCKED = PIPE == 3 || PIPE == 4;
+    const long long total = BLOCKED
         ? (long long)((p.n_elec + wpb - 1) / wpb) * p.groups * wpb : p.items;
     for (long long item = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); item < total;
          item += nwarps) {
         int slot, grp;
-        if constexpr (PIPE == 3) {
+        bool dummy = false;          // PIPE 4: a padding warp that keeps the block in step
+        if constexpr (BLOCKED) {
             const long long blk = item / wpb;
             const long long eb = blk / p.groups;
             grp = (int)(blk - eb * p.groups);
             slot = (int)(eb * wpb + (item - blk * wpb));
-            if (slot >= p.n_elec) continue;                 // warp-uniform
+            if (slot >= p.n_elec) {                          // warp-uniform
+                if constexpr (PIPE == 3) continue;
+                dummy = true;
+                slot = p.n_elec - 1;
+            }
         } else {
             slot = (int)(item / p.groups);
             grp = (int)(item - (long long)slot * p.groups);
@@ -135,19 +144,26 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 
         __syncwarp();                      // previous item's readers are done with the slice
         float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
-        constexpr bool EARLY = PIPE == 1 || PIPE == 3;   // first loads before the weights
+        constexpr bool EARLY = PIPE == 1 || PIPE == 3 || PIPE == 4;   // first loads before the weights
         const int bad = EARLY ? stencil_geometry_warp<GEO>(p, e, lane, ws, t0, t1, t2, slot)
                               : stencil_setup_warp<GEO>(p, e, lane, ws, slot);
-        if (bad && lane == 0) atomicOr(p.status, bad);
+        if (bad && lane == 0 && !dummy) atomicOr(p.status, bad);
         if (bad & BLIP_STATUS_NONFINITE_POS) {
+            if constexpr (PIPE == 4) {
+                // stay in step with the block: contract harmless rows, store NaN
+                if (lane < 16) ws.colrow[lane] = 0;
+                t0 = t1 = t2 = 0.0f;
+                __syncwarp();
+            } else {
 #pragma unroll
-            for (int c = 0; c < CPW; ++c)
+                for (int c = 0; c < CPW; ++c)
 #pragma unroll
-                for (int k = 0; k < NW; ++k)
+                    for (int k = 0; k < NW; ++k)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[c][k][v] = __int_as_float(0x7fc00000);
-            store_outputs<CPW, VEC, VONLY, GEO>(p, e, grp, lane, acc, ws);
-            continue;
+                        for (int v = 0; v < VEC; ++v) acc[c][k][v] = __int_as_float(0x7fc00000);
+                store_outputs<CPW, VEC, VONLY, GEO>(p, e, grp, lane, acc, ws);
+                continue;
+            }
         }
 
         size_t coff[CPW];
@@ -191,7 +207,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                 }
                 contract_rows<T, CPW, VEC, VONLY, RB>(ws, (b + 1) * RB, b1, acc);
             }
-        } else if constexpr (PIPE == 1 || PIPE == 3) {
+        } else if constexpr (PIPE == 1 || PIPE == 3 || PIPE == 4) {
             // software-pipelined: the next batch of RB rows is in flight while
             // the current batch is contracted (two register buffers)
             constexpr int RB = CPW == 1 ? 8 : (CPW == 2 ? 4 : 2);
@@ -201,11 +217,12 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
             for (int r = 0; r < RB; ++r) {
                 const char *rp = tbase + (size_t)(ws.colrow[r >> 2] + (r & 3)) * rowb;
 #pragma unroll
-                for (int c = 0; c < CPW; ++c) buf[0][r][c] = load_row<PIPE == 3>(rp + coff[c]);
+                for (int c = 0; c < CPW; ++c) buf[0][r][c] = load_row<BLOCKED>(rp + coff[c]);
             }
             stencil_weights_warp(p, t0, t1, t2, lane, ws);   // overlaps the first loads
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
+                if constexpr (PIPE == 4) __syncthreads();
                 if (b + 1 < NB) {
 #pragma unroll
                     for (int r = 0; r < RB; ++r) {
@@ -213,7 +230,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                         const char *rp = tbase + (size_t)(ws.colrow[pt >> 2] + (pt & 3)) * rowb;
 #pragma unroll
                         for (int c = 0; c < CPW; ++c)
-                            buf[(b + 1) & 1][r][c] = load_row<PIPE == 3>(rp + coff[c]);
+                            buf[(b + 1) & 1][r][c] = load_row<BLOCKED>(rp + coff[c]);
                     }
                 }
 #pragma unroll
@@ -276,6 +293,17 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                     }
             }
         }
+        if constexpr (PIPE == 4) {
+            if (dummy) continue;
+            if (bad & BLIP_STATUS_NONFINITE_POS) {
+#pragma unroll
+                for (int c = 0; c < CPW; ++c)
+#pragma unroll
+                    for (int k = 0; k < NW; ++k)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[c][k][v] = __int_as_float(0x7fc00000);
+            }
+        }
         store_outputs<CPW, VEC, VONLY, GEO>(p, e, grp, lane, acc, ws);
     }
 }
@@ -283,7 +311,8 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 template <typename T, int CPW, bool VONLY, int GEO>
 void launch_pipe(const EvalParams &p, int pipe, dim3 g, dim3 b, size_t smem, cudaStream_t stream)
 {
-    if (pipe == 3) blip_eval_register<T, CPW, VONLY, 3, GEO><<<g, b, smem, stream>>>(p);
+    if (pipe == 4) blip_eval_register<T, CPW, VONLY, 4, GEO><<<g, b, smem, stream>>>(p);
+    else if (pipe == 3) blip_eval_register<T, CPW, VONLY, 3, GEO><<<g, b, smem, stream>>>(p);
     else if (pipe == 2) blip_eval_register<T, CPW, VONLY, 2, GEO><<<g, b, smem, stream>>>(p);
     else if (pipe == 1) blip_eval_register<T, CPW, VONLY, 1, GEO><<<g, b, smem, stream>>>(p);
     else blip_eval_register<T, CPW, VONLY, 0, GEO><<<g, b, smem, stream>>>(p);
@@ -296,7 +325,7 @@ cudaError_t launch_register_t(const EvalParams &p, int warps, int pipe, cudaStre
     long long blocks = (p.items + warps - 1) / warps;
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    if (pipe == 3) {                 // whole blocks of consecutive electrons per chunk group
+    if (pipe >= 3) {                 // whole blocks of consecutive electrons per chunk group
         blocks = (long long)((p.n_elec + warps - 1) / warps) * p.groups;
         if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
     }

@@ -95,7 +95,7 @@ def test_kernel_configs_bitwise_identical(pb):
     pos = _edge_positions(lat, grid, rng)
     t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
     ref = gpu_eval(t, pos)
-    cfgs = [(v, c, w, s) for v in (1, 3, 4, 6) for c in (1, 2, 3) for w in (1, 4, 16) for s in (0, 1)]
+    cfgs = [(v, c, w, s) for v in (1, 3, 4, 6, 7) for c in (1, 2, 3) for w in (1, 4, 16) for s in (0, 1)]
     cfgs += [(5, g, w, 1) for g in (2, 4) for w in (1, 4, 8)]
     cfgs += [(2, tw, st, s) for tw in (1, 2, 4, 6, 8) for st in (2, 3, 8) for s in (0, 1)]
     for cfg in cfgs:
@@ -129,7 +129,8 @@ def test_grouped_kernel_on_dense_cells(pb, storage):
     t.set_kernel(1, 1, 8, 0)
     ref = gpu_eval(t, pos)
     t.status()
-    for cfg in [(5, 2, 4, 1), (5, 4, 8, 1), (5, 4, 1, 1), (5, 2, 8, 1)]:
+    for cfg in [(5, 2, 4, 1), (5, 4, 8, 1), (5, 4, 1, 1), (5, 2, 8, 1), (7, 1, 4, 1), (7, 1, 8, 0),
+                (6, 1, 4, 1)]:
         t.set_kernel(*cfg)
         for vo in (False, True):
             out = gpu_eval(t, pos, values_only=vo)
@@ -307,7 +308,7 @@ def test_autotune_keeps_results(pb):
     ref = gpu_eval(t, pos)
     dpos = torch.from_numpy(pos).cuda()
     ch = t.autotune(dpos)
-    assert 1 <= ch[0] <= 6 and 1 <= ch[1] <= 8
+    assert 1 <= ch[0] <= 7 and 1 <= ch[1] <= 8
     out = gpu_eval(t, pos)
     for a, b in zip(ref, out):
         assert np.array_equal(a, b)
