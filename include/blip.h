@@ -186,13 +186,19 @@ int blip_info(blip_table t, long long out[8]);
  *                 electrons of one chunk group and the row loads cached in
  *                 L1 (shares rows between neighbours of a sorted batch);
  *              7: as 6, the warps of a block stepping through the row
- *                 batches in lockstep (one block barrier per batch)
+ *                 batches in lockstep (one block barrier per batch);
+ *              8: staged tiles for dense batches (always sorts): the union
+ *                 of the stencil rows of 2 x 2 x chunks grid cells is copied
+ *                 into shared memory once (cp.async.bulk, one 512-byte chunk
+ *                 of components at a time) and every electron of those
+ *                 cells is contracted from there; not with k-points
  *   chunks     variants 1, 3, 4, 6, 7: orbital chunks (32 lanes x 16 bytes) per
  *              warp, 1..3 (1 for 16-bit storage); variant 2: consumer warps
- *              per CTA, 1..8; variant 5: electrons per group, 2 or 4
+ *              per CTA, 1..8; variant 5: electrons per group, 2 or 4;
+ *              variant 8: tile cells along a_3, 2 or 4
  *   warps      variants 1, 3, 4, 6, 7: warps per block, 1..16; variant 2:
  *              shared-memory pipeline stages, 2..32; variant 5: warps per
- *              block, 1..8
+ *              block, 1..8; variant 8: 16 (consumer warps per CTA)
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2
  *              reuse for large batches)
  * Errors: INVALID_ARG for values outside those sets.
@@ -226,8 +232,8 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
  *            koffs[n_k] = n_orb
  * The phase uses the unwrapped fractional coordinates, reduced mod 1 in
  * FP64.  Errors: INVALID_ARG, UNSUPPORTED_DTYPE (real tables).  The bulk-copy
- * kernel (variant 2) has no Bloch epilogue and is not used while k-points
- * are set.
+ * and staged-tile kernels (variants 2 and 8) have no Bloch epilogue and are
+ * not used while k-points are set.
  */
 int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koffs);
 
@@ -281,8 +287,8 @@ int blip_sm_update(int n_walkers, int n, float *dinv, const float *rows, const i
 
 /*
  * blip_test_stall_pipeline - test hook for the failure path (no counterpart
- * in the paper).  With on != 0, launches of the bulk-copy kernel (variant 2)
- * on this table stall their own pipeline: the consumer warps never release
+ * in the paper).  With on != 0, launches of the bulk-copy and staged-tile
+ * kernels (variants 2 and 8) on this table stall their own pipeline: the consumer warps never release
  * the first stage, so the producer's bounded wait runs out, it drains the
  * copies it has in flight, and the consumers' bounded waits run out too.
  * The launch returns after a few seconds with BLIP_STATUS_TIMEOUT set and

@@ -33,6 +33,7 @@ def _sources():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + \
+        glob.glob(os.path.join(CSRC, "*.cuh")) + \
         [os.path.join(HERE, "..", "include", "blip.h"), __file__]
 
 

@@ -55,6 +55,9 @@ struct blip_table_s {
     size_t scratch_bytes = 0;
     // test hook: stall the bulk kernel's pipeline (bounded waits run out)
     int test_stall = 0;
+    // tensor maps of the table for the staged-tile kernel (tile depth 2, 4)
+    TmaDesc tmap[2] = {};
+    bool tmap_ok[2] = {false, false};
     // Bloch k-points (complex tables)
     int n_k = 0;
     int koff[kMaxKpoints + 1] = {};
@@ -205,6 +208,19 @@ int sorted_order(blip_table_s *t, const double *pos, int n_elec, cudaStream_t st
     return BLIP_OK;
 }
 
+// The table's tensor map for the staged-tile kernel with tile depth tz
+// (encoded once, on first use).
+int staged_tmap(blip_table_s *t, int tz, const TmaDesc **out)
+{
+    const int i = tz == 2 ? 0 : 1;
+    if (!t->tmap_ok[i]) {
+        CK(make_staged_tmap(t->d_table, t->elem, t->row_stride, t->rows, tz, &t->tmap[i]));
+        t->tmap_ok[i] = true;
+    }
+    *out = &t->tmap[i];
+    return BLIP_OK;
+}
+
 int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs, int n_walkers,
                 void *values, void *grads, void *laps, cudaStream_t stream, const KernelChoice &kc)
 {
@@ -216,13 +232,15 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
     p.Lreal = t->Lreal;
     p.nchunk = t->nchunk;
     const bool grouped = kc.variant == VAR_GROUPED;
-    p.groups = grouped ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
+    const bool staged = kc.variant == VAR_STAGED;
+    p.groups = (grouped || staged) ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
     p.items = (long long)n_elec * p.groups;
     p.geo = t->geo;
     p.pos = pos;
     p.n_elec = n_elec;
     p.perm = nullptr;
-    if (kc.sort || grouped) {
+    if (staged && t->n_k) return BLIP_ERR_INVALID_ARG;    // no Bloch epilogue in this kernel
+    if (kc.sort || grouped || staged) {
         int *perm = nullptr;
         const ElecGeo *rec = nullptr;
         const bool want_rec = t->n_k == 0 && kc.variant != VAR_BULK;
@@ -250,6 +268,13 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
         const int *keys = nullptr, *cell_end = nullptr;
         sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
         CK(launch_grouped(p, t->elem, kc.chunks, kc.warps, keys, cell_end, stream));
+    } else if (staged) {
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
+        const TmaDesc *tm = nullptr;
+        int rc = staged_tmap(t, kc.chunks, &tm);
+        if (rc) return rc;
+        CK(launch_staged(p, t->elem, kc.chunks, cell_end, *tm, t->sm_count, t->test_stall, stream));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
     }
@@ -562,6 +587,11 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         // chunks = electrons per group (2 or 4); always evaluated in cell order
         if ((chunks != 2 && chunks != 4) || warps < 1 || warps > 8) return BLIP_ERR_INVALID_ARG;
         sort = 1;
+    } else if (variant == VAR_STAGED) {
+        // chunks = tile cells along a_3 (2 or 4); 16 consumer warps per CTA
+        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
+        if ((chunks != 2 && chunks != 4) || warps != 16) return BLIP_ERR_INVALID_ARG;
+        sort = 1;
     } else if (variant == VAR_BULK) {
         if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
         // chunks = consumer warps per CTA (chunks per tile), warps = pipeline stages
@@ -607,6 +637,8 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
         if (srt)
             for (int g : {2, 4})
                 for (int w : {4, 8}) cands.push_back(KernelChoice{VAR_GROUPED, g, w, 1});
+        if (srt && !t->n_k)
+            for (int tz : {2, 4}) cands.push_back(KernelChoice{VAR_STAGED, tz, 16, 1});
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -688,9 +720,12 @@ int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koff
         }
     for (int q = 0; q <= n_k; ++q) t->koff[q] = koffs[q];
     t->n_k = n_k;
-    if (t->choice.variant == VAR_BULK) t->choice = KernelChoice{VAR_REGISTER, 1, 8, 0};
+    auto has_bloch = [](const KernelChoice &kc) {
+        return kc.variant != VAR_BULK && kc.variant != VAR_STAGED;
+    };
+    if (!has_bloch(t->choice)) t->choice = KernelChoice{VAR_REGISTER, 1, 8, 0};
     for (auto &kv : t->tuned)
-        if (kv.second.variant == VAR_BULK) kv.second = KernelChoice{VAR_REGISTER, 1, 8, 0};
+        if (!has_bloch(kv.second)) kv.second = KernelChoice{VAR_REGISTER, 1, 8, 0};
     return BLIP_OK;
 }
 
@@ -861,7 +896,8 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
     p.Lreal = t->Lreal;
     p.nchunk = t->nchunk;
     const bool grouped = kc.variant == VAR_GROUPED;
-    p.groups = grouped ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
+    const bool staged = kc.variant == VAR_STAGED;
+    p.groups = (grouped || staged) ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
     p.items = (long long)n_elec * p.groups;
     p.geo = t->geo;
     p.pos = pos;
@@ -886,6 +922,14 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
         const int *keys = nullptr, *cell_end = nullptr;
         sort_views(t->geo, n_elec, scratch, &keys, &cell_end);
         CK(launch_grouped(p, t->elem, kc.chunks, kc.warps, keys, cell_end, s));
+    } else if (staged) {
+        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, n_elec, scratch, &keys, &cell_end);
+        const TmaDesc *tm = nullptr;
+        rc = staged_tmap(t, kc.chunks, &tm);
+        if (rc) return rc;
+        CK(launch_staged(p, t->elem, kc.chunks, cell_end, *tm, t->sm_count, t->test_stall, s));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, s));
     }

@@ -20,7 +20,9 @@ enum Variant {
     VAR_GROUPED = 5,          // electrons of one cell share each row load (sorted)
     VAR_REGISTER_L1 = 6,      // double-buffered; a block's warps take consecutive
                               // electrons of one chunk group and share rows via L1
-    VAR_REGISTER_LOCKSTEP = 7 // as 6, the block's warps in lockstep per row batch
+    VAR_REGISTER_LOCKSTEP = 7,// as 6, the block's warps in lockstep per row batch
+    VAR_STAGED = 8            // 2 x 2 x TZ cell tiles: union rows staged in shared
+                              // memory, every electron of the tile contracted there
 };
 
 constexpr int kMaxKpoints = 16;
@@ -120,6 +122,25 @@ void sort_views(const Geometry &geo, int n_elec, void *scratch, const int **keys
 // together, reading each stencil row once for the whole group.
 cudaError_t launch_grouped(const EvalParams &p, int elem, int group, int warps, const int *keys,
                            const int *cell_end, cudaStream_t stream);
+
+// Opaque 128-byte tensor-map (TMA descriptor) storage.
+struct alignas(64) TmaDesc {
+    unsigned long long w[16];
+};
+
+// Tensor map of a stored table for the staged-tile kernel with tile depth tz:
+// the table as a 2-D tensor [rows][row_stride] of its element, box = one
+// 512-byte chunk x (tz + 3) rows.  Returns cudaSuccess or an error.
+cudaError_t make_staged_tmap(const void *table, int elem, long long row_stride, long long rows,
+                             int tz, TmaDesc *out);
+
+// Launch the staged-tile kernel (needs the sort): tiles of 2 x 2 x tz cells
+// (tz = 2 or 4), the union of their stencil rows copied into shared memory
+// chunk by chunk, all electrons of a tile contracted from there.  tmap comes
+// from make_staged_tmap for the same table and tz.  stall != 0 is the same
+// test hook as for launch_bulk.
+cudaError_t launch_staged(const EvalParams &p, int elem, int tz, const int *cell_end,
+                          const TmaDesc &tmap, int sm_count, int stall, cudaStream_t stream);
 
 // Sherman-Morrison update of n_walkers inverses after one accepted move each
 // (blip_sm.cu); work holds [n_walkers][2 n] floats.

@@ -75,5 +75,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+// Tiled tensor copy (TMA) of one 2-D box at element coordinates (c0, c1)
+// of the tensor map at tmap (a kernel parameter) into shared memory.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int c0, int c1,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+
 }  // namespace mb
 }  // namespace blip

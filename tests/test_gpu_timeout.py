@@ -1,6 +1,6 @@
-"""The bounded waits of the bulk-copy kernel: a stalled pipeline (test hook,
-the consumers never release the first stage) makes the waits run out after
-about two seconds; the kernel returns, reports BLIP_STATUS_TIMEOUT, and the
+"""The bounded waits of the bulk-copy and staged-tile kernels: a stalled
+pipeline (test hook, the consumers never release the first stage) makes the
+waits run out after about two seconds; the kernel returns, reports BLIP_STATUS_TIMEOUT, and the
 same context evaluates correctly afterwards.  No fault, trap or unbounded
 spin is involved."""
 import time
@@ -24,13 +24,15 @@ def pb():
     return pb
 
 
-def test_stalled_pipeline_times_out_and_context_survives(pb):
+@pytest.mark.parametrize("cfg", [(2, 1, 2, 0), (8, 4, 16, 1)])
+def test_stalled_pipeline_times_out_and_context_survives(pb, cfg):
     grid = (8, 8, 8)
     lat = pins.triclinic_lattice()
-    tab = bi.smooth_random_table(grid, 128, seed=61)
+    # 4 chunks per row: every CTA of either kernel fills its first stage again
+    tab = bi.smooth_random_table(grid, 512, seed=61)
     pos = np.random.default_rng(61).uniform(0, 1, size=(64, 3)) @ lat
     t = pb.BlipTable(grid, lat, tab)
-    t.set_kernel(2, 1, 2, 0)                 # bulk copy, 2 stages
+    t.set_kernel(*cfg)                       # bulk copy with 2 stages, or staged tiles
     t.status()
     pb.lib().blip_test_stall_pipeline(t.handle, 1)
     t0 = time.time()
