@@ -198,7 +198,7 @@ int blip_info(blip_table t, long long out[8]);
  *              variant 8: tile cells along a_3, 2 or 4
  *   warps      variants 1, 3, 4, 6, 7: warps per block, 1..16; variant 2:
  *              shared-memory pipeline stages, 2..32; variant 5: warps per
- *              block, 1..8; variant 8: 16 (consumer warps per CTA)
+ *              block, 1..8; variant 8: consumer warps per CTA, 12 or 16
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2
  *              reuse for large batches)
  * Errors: INVALID_ARG for values outside those sets.

@@ -274,7 +274,8 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
         const TmaDesc *tm = nullptr;
         int rc = staged_tmap(t, kc.chunks, &tm);
         if (rc) return rc;
-        CK(launch_staged(p, t->elem, kc.chunks, cell_end, *tm, t->sm_count, t->test_stall, stream));
+        CK(launch_staged(p, t->elem, kc.chunks, kc.warps, cell_end, *tm, t->sm_count, t->test_stall,
+                         stream));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
     }
@@ -588,9 +589,9 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         if ((chunks != 2 && chunks != 4) || warps < 1 || warps > 8) return BLIP_ERR_INVALID_ARG;
         sort = 1;
     } else if (variant == VAR_STAGED) {
-        // chunks = tile cells along a_3 (2 or 4); 16 consumer warps per CTA
+        // chunks = tile cells along a_3 (2 or 4); warps = consumer warps per CTA
         if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
-        if ((chunks != 2 && chunks != 4) || warps != 16) return BLIP_ERR_INVALID_ARG;
+        if ((chunks != 2 && chunks != 4) || (warps != 12 && warps != 16)) return BLIP_ERR_INVALID_ARG;
         sort = 1;
     } else if (variant == VAR_BULK) {
         if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
@@ -638,7 +639,8 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
             for (int g : {2, 4})
                 for (int w : {4, 8}) cands.push_back(KernelChoice{VAR_GROUPED, g, w, 1});
         if (srt && !t->n_k)
-            for (int tz : {2, 4}) cands.push_back(KernelChoice{VAR_STAGED, tz, 16, 1});
+            for (int tz : {2, 4})
+                for (int cw : {12, 16}) cands.push_back(KernelChoice{VAR_STAGED, tz, cw, 1});
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -929,7 +931,8 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
         const TmaDesc *tm = nullptr;
         rc = staged_tmap(t, kc.chunks, &tm);
         if (rc) return rc;
-        CK(launch_staged(p, t->elem, kc.chunks, cell_end, *tm, t->sm_count, t->test_stall, s));
+        CK(launch_staged(p, t->elem, kc.chunks, kc.warps, cell_end, *tm, t->sm_count, t->test_stall,
+                         s));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, s));
     }

@@ -136,10 +136,10 @@ cudaError_t make_staged_tmap(const void *table, int elem, long long row_stride, 
 
 // Launch the staged-tile kernel (needs the sort): tiles of 2 x 2 x tz cells
 // (tz = 2 or 4), the union of their stencil rows copied into shared memory
-// chunk by chunk, all electrons of a tile contracted from there.  tmap comes
-// from make_staged_tmap for the same table and tz.  stall != 0 is the same
-// test hook as for launch_bulk.
-cudaError_t launch_staged(const EvalParams &p, int elem, int tz, const int *cell_end,
+// chunk by chunk, all electrons of a tile contracted from there by cw (12 or
+// 16) consumer warps.  tmap comes from make_staged_tmap for the same table
+// and tz.  stall != 0 is the same test hook as for launch_bulk.
+cudaError_t launch_staged(const EvalParams &p, int elem, int tz, int cw, const int *cell_end,
                           const TmaDesc &tmap, int sm_count, int stall, cudaStream_t stream);
 
 // Sherman-Morrison update of n_walkers inverses after one accepted move each

@@ -25,13 +25,17 @@
 //     stages a third of the time; with one box per column the producer
 //     mostly waits for free stages.)  It also asks L2 to prefetch the whole
 //     union rows of its next tile, so that those copies hit in L2.
-//   * consumers: per part, form the combined weights of its electrons in
-//     shared memory (electron j by warp j mod 16), then per stage contract
-//     them (one warp per electron, 16 bytes of each row per lane, 5 FMAs per
-//     component and site in the same site order as the register kernels, so
-//     results are bitwise identical) and store the outputs.  Electrons go to
-//     warps round robin, the rotation carried from stage to stage, so the
-//     warps of a CTA stay level within a part.
+//   * consumers (CW = 12 or 16 warps): per part, form the combined weights
+//     of its electrons in shared memory (electron j by warp j mod CW), then
+//     per stage contract them (one warp per electron, 16 bytes of each row
+//     per lane, 5 FMAs per component and site in the same site order as the
+//     register kernels, so results are bitwise identical) and store the
+//     outputs.  Electrons go to warps round robin, the rotation carried from
+//     stage to stage, so the warps of a CTA stay level within a part and
+//     drift across at most two stages (handing the electrons out from a
+//     shared counter instead kept the warps in step at every stage boundary
+//     and was measured about 9 % slower; pairing electrons of one cell to share
+//     row loads gained nothing measurable).
 // The electrons of a tile are four contiguous slot ranges of the sorted
 // order (one per (a_1, a_2) column of the tile: the brick-major sort key
 // runs along a_3 fastest); positions without a cell sit in the last bucket
@@ -55,7 +59,6 @@ using namespace mb;
 constexpr int kTX = 2, kTY = 2;                  // tile cells along a_1, a_2
 constexpr int kCX = kTX + 3, kCY = kTY + 3;      // union columns along a_1, a_2
 constexpr int kSlice = 512;                      // bytes of one row per stage
-constexpr int kCW = 16;                          // consumer warps
 
 // Ring depth and electrons per part: the smaller TZ = 2 stages leave room
 // for a third stage (a deeper pipeline) at the price of smaller parts.
@@ -217,7 +220,9 @@ __device__ __forceinline__ void contract_electron(const EvalParams &p, const Ele
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[k][v] = 0.0f;
     const unsigned char *sb = stage + (size_t)w.base * kSlice + lane * 16;
-#pragma unroll
+    // 16-bit tables keep the a_1 loop rolled: fully unrolled, with the 8-wide
+    // unpacking and accumulators, it was measured about 30 % slower
+#pragma unroll(sizeof(T) == 4 ? 4 : 1)
     for (int kx = 0; kx < 4; ++kx)
 #pragma unroll
         for (int ky = 0; ky < 4; ++ky)
@@ -247,13 +252,14 @@ __device__ __forceinline__ void contract_electron(const EvalParams &p, const Ele
     store_chunk<VEC, VONLY>(p, w.e, chunk, lane, acc);
 }
 
+template <int CW>
 __device__ __forceinline__ void consumer_sync()
 {
-    asm volatile("bar.sync 1, %0;" ::"r"(kCW * 32) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(CW * 32) : "memory");
 }
 
-template <typename T, int TZ, bool VONLY>
-__global__ void __launch_bounds__(32 * (kCW + 1), 1)
+template <typename T, int TZ, bool VONLY, int CW>
+__global__ void __launch_bounds__(32 * (CW + 1), 1)
     blip_eval_staged(EvalParams p, StagedArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int VEC = Elt<T>::VEC;
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(32 * (kCW + 1), 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full + s, 1);
-            mbar_init(empty + s, kCW);
+            mbar_init(empty + s, CW);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(32 * (kCW + 1), 1)
     __syncthreads();
 
     const int n1 = p.geo.n[0], n2 = p.geo.n[1], n3 = p.geo.n[2];
-    if (warp == kCW) {
+    if (warp == CW) {
         // ---------------- producer ----------------
         const char *tbase = reinterpret_cast<const char *>(p.table);
         const size_t rowb = (size_t)p.row_stride * sizeof(T);
@@ -355,8 +361,8 @@ __global__ void __launch_bounds__(32 * (kCW + 1), 1)
     // positions without a cell (last sort bucket): NaN outputs
     {
         const int nan0 = a.cell_end[a.P - 1];
-        for (long long sl = nan0 + (long long)blockIdx.x * kCW + cw; sl < p.n_elec;
-             sl += (long long)gridDim.x * kCW) {
+        for (long long sl = nan0 + (long long)blockIdx.x * CW + cw; sl < p.n_elec;
+             sl += (long long)gridDim.x * CW) {
             const int e = p.perm[sl];
             if (lane == 0) {
                 int bad = BLIP_STATUS_NONFINITE_POS;
@@ -383,10 +389,10 @@ __global__ void __launch_bounds__(32 * (kCW + 1), 1)
         for (int part = 0; part < parts; ++part) {
             const int q0 = (int)((long long)part * ti.n / parts);
             const int cnt = (int)((long long)(part + 1) * ti.n / parts) - q0;
-            consumer_sync();   // the previous part's weights are no longer read
+            consumer_sync<CW>();   // the previous part's weights are no longer read
             if (!*abort_flag)
-                for (int j = cw; j < cnt; j += kCW) setup_electron<TZ>(p, ti, q0 + j, lane, W[j]);
-            consumer_sync();
+                for (int j = cw; j < cnt; j += CW) setup_electron<TZ>(p, ti, q0 + j, lane, W[j]);
+            consumer_sync<CW>();
             for (int o = 0; o < p.nchunk; ++o) {
                 const int s = (int)(fill % kStages);
                 bool have = false;
@@ -400,19 +406,19 @@ __global__ void __launch_bounds__(32 * (kCW + 1), 1)
                 }
                 if (have) {
                     const unsigned char *st = stage0 + s * SB;
-                    for (int j = (cw - rot + kCW) % kCW; j < cnt; j += kCW)
+                    for (int j = (cw - rot + CW) % CW; j < cnt; j += CW)
                         contract_electron<T, TZ, VONLY>(p, W[j], st, o, lane);
                 }
                 __syncwarp();
                 if (lane == 0 && !(a.stall && fill == 0)) mbar_arrive(empty + s);
-                rot = (rot + cnt) % kCW;
+                rot = (rot + cnt) % CW;
                 ++fill;
             }
         }
     }
 }
 
-template <typename T, int TZ, bool VONLY>
+template <typename T, int TZ, bool VONLY, int CW>
 cudaError_t launch_staged_t(const EvalParams &p, StagedArgs a, const CUtensorMap &tmap, int sm_count,
                             cudaStream_t stream)
 {
@@ -420,7 +426,7 @@ cudaError_t launch_staged_t(const EvalParams &p, StagedArgs a, const CUtensorMap
     static_assert(smem <= 227 * 1024, "stage ring and weights exceed shared memory");
     static bool attr_set = false;   // raise this instantiation's dynamic shared-memory cap once
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(blip_eval_staged<T, TZ, VONLY>,
+        cudaError_t e = cudaFuncSetAttribute(blip_eval_staged<T, TZ, VONLY, CW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
@@ -429,20 +435,28 @@ cudaError_t launch_staged_t(const EvalParams &p, StagedArgs a, const CUtensorMap
     a.ntz = (p.geo.n[2] + TZ - 1) / TZ;
     a.ntiles = ((p.geo.n[0] + kTX - 1) / kTX) * a.nty * a.ntz;
     const int grid = std::max(1, std::min(sm_count, a.ntiles));
-    blip_eval_staged<T, TZ, VONLY><<<grid, 32 * (kCW + 1), smem, stream>>>(p, a, tmap);
+    blip_eval_staged<T, TZ, VONLY, CW><<<grid, 32 * (CW + 1), smem, stream>>>(p, a, tmap);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_staged_elem(const EvalParams &p, const StagedArgs &a, int tz,
-                               const CUtensorMap &tm, int sm_count, cudaStream_t stream)
+template <typename T, int CW>
+cudaError_t launch_staged_cw(const EvalParams &p, const StagedArgs &a, int tz,
+                             const CUtensorMap &tm, int sm_count, cudaStream_t stream)
 {
     const bool vonly = p.grads == nullptr;
     if (tz == 2)
-        return vonly ? launch_staged_t<T, 2, true>(p, a, tm, sm_count, stream)
-                     : launch_staged_t<T, 2, false>(p, a, tm, sm_count, stream);
-    return vonly ? launch_staged_t<T, 4, true>(p, a, tm, sm_count, stream)
-                 : launch_staged_t<T, 4, false>(p, a, tm, sm_count, stream);
+        return vonly ? launch_staged_t<T, 2, true, CW>(p, a, tm, sm_count, stream)
+                     : launch_staged_t<T, 2, false, CW>(p, a, tm, sm_count, stream);
+    return vonly ? launch_staged_t<T, 4, true, CW>(p, a, tm, sm_count, stream)
+                 : launch_staged_t<T, 4, false, CW>(p, a, tm, sm_count, stream);
+}
+
+template <typename T>
+cudaError_t launch_staged_elem(const EvalParams &p, const StagedArgs &a, int tz, int cw,
+                               const CUtensorMap &tm, int sm_count, cudaStream_t stream)
+{
+    return cw == 12 ? launch_staged_cw<T, 12>(p, a, tz, tm, sm_count, stream)
+                    : launch_staged_cw<T, 16>(p, a, tz, tm, sm_count, stream);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -483,10 +497,11 @@ cudaError_t make_staged_tmap(const void *table, int elem, long long row_stride, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_staged(const EvalParams &p, int elem, int tz, const int *cell_end,
+cudaError_t launch_staged(const EvalParams &p, int elem, int tz, int cw, const int *cell_end,
                           const TmaDesc &tmap, int sm_count, int stall, cudaStream_t stream)
 {
-    if ((tz != 2 && tz != 4) || !p.perm || !cell_end || p.n_k) return cudaErrorInvalidValue;
+    if ((tz != 2 && tz != 4) || (cw != 12 && cw != 16) || !p.perm || !cell_end || p.n_k)
+        return cudaErrorInvalidValue;
     StagedArgs a{};
     a.cell_end = cell_end;
     a.nty = (p.geo.n[1] + kTY - 1) / kTY;
@@ -495,9 +510,9 @@ cudaError_t launch_staged(const EvalParams &p, int elem, int tz, const int *cell
     a.stall = stall;
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(&tmap);
     switch (elem) {
-    case ELEM_F32: return launch_staged_elem<float>(p, a, tz, tm, sm_count, stream);
-    case ELEM_BF16: return launch_staged_elem<__nv_bfloat16>(p, a, tz, tm, sm_count, stream);
-    case ELEM_F16: return launch_staged_elem<__half>(p, a, tz, tm, sm_count, stream);
+    case ELEM_F32: return launch_staged_elem<float>(p, a, tz, cw, tm, sm_count, stream);
+    case ELEM_BF16: return launch_staged_elem<__nv_bfloat16>(p, a, tz, cw, tm, sm_count, stream);
+    case ELEM_F16: return launch_staged_elem<__half>(p, a, tz, cw, tm, sm_count, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -77,15 +77,15 @@ def test_staged_matches_register_kernel_and_oracle(pb, grid, n_orb, storage):
     ref = gpu_eval(t, pos)
     ref_vo = gpu_eval(t, pos, values_only=True)
     t.status()
-    for tz in (2, 4):
-        t.set_kernel(8, tz, 16, 1)
+    for tz, cw in ((2, 16), (4, 16), (2, 12), (4, 12)):
+        t.set_kernel(8, tz, cw, 1)
         out = gpu_eval(t, pos)
         for a, b in zip(ref, out):
-            assert np.array_equal(a, b, equal_nan=True), tz
+            assert np.array_equal(a, b, equal_nan=True), (tz, cw)
         st = t.status()
         assert st & pb.STATUS_NONFINITE_POS and st & pb.STATUS_FAR_POS
         vo = gpu_eval(t, pos, values_only=True)
-        assert np.array_equal(ref_vo[0], vo[0], equal_nan=True), tz
+        assert np.array_equal(ref_vo[0], vo[0], equal_nan=True), (tz, cw)
         t.status()
     bad = ~np.isfinite(pos).all(1)
     assert np.isnan(ref[0][bad]).all() and np.isnan(ref[1][bad]).all()
@@ -104,11 +104,11 @@ def test_staged_with_walker_offsets_and_ragged_batches(pb):
     t = pb.BlipTable(grid, lat, tab)
     t.set_kernel(3, 1, 8, 0)
     ref = gpu_eval(t, pos, offsets=offs)
-    for tz in (2, 4):
-        t.set_kernel(8, tz, 16, 1)
+    for tz, cw in ((2, 16), (4, 12)):
+        t.set_kernel(8, tz, cw, 1)
         out = gpu_eval(t, pos, offsets=offs)
         for a, b in zip(ref, out):
-            assert np.array_equal(a, b), tz
+            assert np.array_equal(a, b), (tz, cw)
     assert t.status() == 0
     bad = offs.copy()
     bad[3] = bad[2] - 1
@@ -143,9 +143,10 @@ def _sample(n, k, seed):
     return np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, size=k)]))
 
 
-@pytest.mark.parametrize("name,storage,tz", [("tio2_batch", "f32", 4), ("tio2_batch", "f32", 2),
-                                             ("tio2_precision", "bf16", 4)])
-def test_staged_full_size_tio2(pb, name, storage, tz):
+@pytest.mark.parametrize("name,storage,tz,cw", [("tio2_batch", "f32", 4, 12),
+                                                ("tio2_batch", "f32", 2, 16),
+                                                ("tio2_precision", "bf16", 4, 16)])
+def test_staged_full_size_tio2(pb, name, storage, tz, cw):
     """Full-size TiO2-shaped table (72 x 72 x 48, 768 orbitals): 256 walkers x
     1,536 moved electrons, or 64 walkers of the precision workload in BF16;
     sampled electrons against the oracle, a slice against the register
@@ -157,7 +158,7 @@ def test_staged_full_size_tio2(pb, name, storage, tz):
     t = pb.BlipTable(wl.grid, wl.lattice, tab, storage=kind)
     dpos = torch.from_numpy(pos).cuda()
     doffs = torch.from_numpy(offs).cuda()
-    t.set_kernel(8, tz, 16, 1)
+    t.set_kernel(8, tz, cw, 1)
     v, g, lp = t.eval(dpos, doffs)
     torch.cuda.synchronize()
     assert t.status() == 0
