@@ -112,10 +112,13 @@ def touched_sites(grid, lattice, pos):
 
 
 def kernel_hash():
+    """SHA-256 (16 hex digits) of every CUDA source of the library."""
     h = hashlib.sha256()
-    for f in ("blip_eval.cu", "blip_bulk.cu", "blip_device.cuh", "blip_internal.h"):
-        with open(os.path.join(ROOT, "paper_1204_1121_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_1204_1121_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
