@@ -37,7 +37,10 @@ import blip_inputs as bi  # noqa: E402
 # changes.  Filled from the committed summary under profiles/.
 NCU_TRAFFIC = {
     # (kernel source hash, workload, storage, electrons): (variant, chunks, bytes)
-    ("db994e9e1f6f1089", "tio2", "f32", 1536): (3, 2, 274803712 + 11272192),
+    ("ebb4fc4e908d3f58", "tio2", "f32", 1536): (3, 2, 274782464 + 11627520),
+    # captured with 128 orbitals, scaled x6 to 768 (rows and outputs grow
+    # in proportion to the orbital count)
+    ("ebb4fc4e908d3f58", "tio2_batch", "f32", 393216): (8, 4, 6 * (156598784 + 946901248)),
 }
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "c64": 3, "bf16pair": 4}

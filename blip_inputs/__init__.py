@@ -324,20 +324,24 @@ def workload(name: str, **kw) -> Workload:
     * ``tio2_super_complex``: 2 x 2 x 2 supercell (34.8 x 34.8 x 22.4 bohr),
       144 x 144 x 96 grid, 1,536 complex orbitals (Fourier-space table
       recipe), 512 walkers with batch sizes uniform in {1..512}.
+
+    The TiO2 workloads take ``n_orb`` to shrink the orbital count (smaller
+    profiling cases with the same positions).
     """
     if name == "cubic16":
         w = Workload(name, cubic_lattice(10.0), (16, 16, 16), 8, table_seed=0, pos_seed=0,
                      uniform_n=64)
     elif name == "tio2":
-        w = Workload(name, TIO2_CELL, TIO2_GRID, 768, table_seed=0, pos_seed=101,
-                     uniform_n=1536)
+        w = Workload(name, TIO2_CELL, TIO2_GRID, kw.pop("n_orb", 768), table_seed=0,
+                     pos_seed=101, uniform_n=1536)
     elif name == "tio2_batch":
         b = kw.pop("batch", 1536)
-        w = Workload(name, TIO2_CELL, TIO2_GRID, 768, table_seed=0, pos_seed=102,
-                     n_walkers=kw.pop("n_walkers", 256), n_per_walker=1536, batch=b)
+        w = Workload(name, TIO2_CELL, TIO2_GRID, kw.pop("n_orb", 768), table_seed=0,
+                     pos_seed=102, n_walkers=kw.pop("n_walkers", 256), n_per_walker=1536, batch=b)
     elif name == "tio2_precision":
-        w = Workload(name, TIO2_CELL, TIO2_GRID, 768, table_seed=0, pos_seed=103,
-                     n_walkers=kw.pop("n_walkers", 1024), n_per_walker=1536, batch=1536)
+        w = Workload(name, TIO2_CELL, TIO2_GRID, kw.pop("n_orb", 768), table_seed=0,
+                     pos_seed=103, n_walkers=kw.pop("n_walkers", 1024), n_per_walker=1536,
+                     batch=1536)
     elif name == "tio2_super_complex":
         w = Workload(name, tetragonal_lattice(34.8, 22.4), (144, 144, 96), kw.pop("n_orb", 1536),
                      is_complex=True, table_seed=0, pos_seed=104,
