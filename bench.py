@@ -198,7 +198,7 @@ def cpu_baseline(w, tab, pos, seconds):
     per_e = probe / min(E, 256)
     n = int(max(64, min(E, seconds / max(per_e, 1e-9))))
     reps = max(1, int(seconds / max(per_e * n, 1e-9)))
-    reps = min(reps, 50)
+    reps = min(reps, 2000)
     t0 = time.perf_counter()
     for _ in range(reps):
         oracle.eval_stencil(w.grid, w.lattice, tab, pos[:n], threads=cores)
