@@ -91,3 +91,28 @@ def test_noalloc_rejects_a_batch_beyond_the_fixed_scratch(pb):
     assert rc == -7
     assert b"no-allocation" in pb.lib().blip_strerror(rc)
     assert bool((v == 7.0).all())
+
+
+def test_noalloc_with_the_staged_tile_kernel(pb):
+    """The staged-tile kernel through the no-allocation entry point (which
+    has no per-electron geometry records, so the kernel wraps the positions
+    itself): bitwise equal to blip_eval with the same kernel, on a dense
+    batch with a non-finite position."""
+    grid = (9, 8, 10)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 200, seed=23)
+    t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
+    pos = bi.uniform_positions(lat, 5000, seed=24)
+    pos[17] = [np.nan, 0.0, 0.0]
+    dpos = torch.from_numpy(pos).cuda()
+    for cfg in [(8, 4, 12, 1), (8, 2, 16, 1)]:
+        t.set_kernel(*cfg)
+        ref = t.eval(dpos)
+        out = t.alloc_outputs(len(pos))
+        rc = _noalloc(pb, t, dpos, None, out)
+        assert rc == 0, pb.lib().blip_strerror(rc)
+        torch.cuda.synchronize()
+        for r, o in zip(ref, out):
+            assert torch.equal(torch.nan_to_num(r, nan=7.0), torch.nan_to_num(o, nan=7.0)), cfg
+        assert bool(torch.isnan(out[0][17]).all())
+        assert t.status() & pb.STATUS_NONFINITE_POS
