@@ -200,7 +200,10 @@ int blip_info(blip_table t, long long out[8]);
  *              shared-memory pipeline stages, 2..32; variant 5: warps per
  *              block, 1..8; variant 8: consumer warps per CTA, 12 or 16
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2
- *              reuse for large batches)
+ *              reuse for large batches); 2 (variants 1, 3, 4): sorted, and
+ *              the warps' work ordered by orbital chunk group first, so the
+ *              warps in flight cover more electrons with a smaller slice of
+ *              each row
  * Errors: INVALID_ARG for values outside those sets.
  */
 int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort);

@@ -249,6 +249,7 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
         p.perm = perm;
         p.georec = rec;
     }
+    p.group_major = kc.sort == 2 ? 1 : 0;
     p.offsets = offs;
     p.n_walkers = offs ? n_walkers : 0;
     p.values = static_cast<float *>(values);
@@ -601,7 +602,11 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
     } else {
         return BLIP_ERR_INVALID_ARG;
     }
-    if (sort != 0 && sort != 1) return BLIP_ERR_INVALID_ARG;
+    // sort 2: sorted, and the register kernels' items ordered chunk group
+    // slowest
+    const bool order_ok = variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE ||
+                          variant == VAR_REGISTER_ROLLED;
+    if (sort != 0 && sort != 1 && !(sort == 2 && order_ok)) return BLIP_ERR_INVALID_ARG;
     t->auto_mode = false;
     t->choice = KernelChoice{variant, chunks, warps, sort};
     return BLIP_OK;
@@ -628,6 +633,11 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
                 cands.push_back(KernelChoice{VAR_REGISTER, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_ROLLED, c, w, srt});
+                if (srt && t->nchunk > c) {       // several chunk groups: try their order too
+                    cands.push_back(KernelChoice{VAR_REGISTER, c, w, 2});
+                    cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, 2});
+                    cands.push_back(KernelChoice{VAR_REGISTER_ROLLED, c, w, 2});
+                }
                 if (srt) cands.push_back(KernelChoice{VAR_REGISTER_L1, c, w, srt});
                 if (srt) cands.push_back(KernelChoice{VAR_REGISTER_LOCKSTEP, c, w, srt});
             }
@@ -905,6 +915,7 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
     p.pos = pos;
     p.n_elec = n_elec;
     p.perm = perm;
+    p.group_major = kc.sort == 2 ? 1 : 0;
     p.offsets = walker_offsets;
     p.n_walkers = walker_offsets ? n_walkers : 0;
     p.values = static_cast<float *>(values);

@@ -55,6 +55,7 @@ struct EvalParams {
     int nchunk;             // 16-byte-per-lane chunks per row: ceil(Lreal / (32 * VEC))
     int groups;             // chunk groups per electron: ceil(nchunk / chunks per warp)
     long long items;        // n_elec * groups
+    int group_major;        // register kernels: items ordered chunk group slowest
     Geometry geo;
     const double *pos;      // [n_elec][3]
     int n_elec;

@@ -128,6 +128,12 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                 dummy = true;
                 slot = p.n_elec - 1;
             }
+        } else if (p.group_major) {
+            // every electron's first chunk group, then the second, ...: the
+            // warps in flight cover more electrons with a smaller slice of
+            // each row, so more of the rows they share stay in L2
+            grp = (int)(item / p.n_elec);
+            slot = (int)(item - (long long)grp * p.n_elec);
         } else {
             slot = (int)(item / p.groups);
             grp = (int)(item - (long long)slot * p.groups);

@@ -99,6 +99,7 @@ def test_kernel_configs_bitwise_identical(pb):
     cfgs += [(5, g, w, 1) for g in (2, 4) for w in (1, 4, 8)]
     cfgs += [(2, tw, st, s) for tw in (1, 2, 4, 6, 8) for st in (2, 3, 8) for s in (0, 1)]
     cfgs += [(8, tz, cw, 1) for tz in (2, 4) for cw in (12, 16)]
+    cfgs += [(v, c, w, 2) for v in (1, 3, 4) for c in (1, 2, 3) for w in (1, 8)]
     for cfg in cfgs:
         t.set_kernel(*cfg)
         out = gpu_eval(t, pos)
