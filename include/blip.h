@@ -191,16 +191,18 @@ int blip_info(blip_table t, long long out[8]);
  *                 of the stencil rows of 2 x 2 x chunks grid cells is copied
  *                 into shared memory once (cp.async.bulk, one 512-byte chunk
  *                 of components at a time) and every electron of those
- *                 cells is contracted from there; not with k-points
+ *                 cells is contracted from there; not with k-points;
+ *              9: as 3 with two row batches in flight (FP32 tables, one
+ *                 chunk per warp)
  *   chunks     variants 1, 3, 4, 6, 7: orbital chunks (32 lanes x 16 bytes) per
- *              warp, 1..3 (1 for 16-bit storage); variant 2: consumer warps
+ *              warp, 1..3 (1 for 16-bit storage); variant 9: 1; variant 2: consumer warps
  *              per CTA, 1..8; variant 5: electrons per group, 2 or 4;
  *              variant 8: tile cells along a_3, 2 or 4
- *   warps      variants 1, 3, 4, 6, 7: warps per block, 1..16; variant 2:
+ *   warps      variants 1, 3, 4, 6, 7, 9: warps per block, 1..16; variant 2:
  *              shared-memory pipeline stages, 2..32; variant 5: warps per
  *              block, 1..8; variant 8: consumer warps per CTA, 12 or 16
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2
- *              reuse for large batches); 2 (variants 1, 3, 4): sorted, and
+ *              reuse for large batches); 2 (variants 1, 3, 4, 9): sorted, and
  *              the warps' work ordered by orbital chunk group first, so the
  *              warps in flight cover more electrons with a smaller slice of
  *              each row

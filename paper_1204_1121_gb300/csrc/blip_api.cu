@@ -580,7 +580,11 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         t->auto_mode = true;
         return BLIP_OK;
     }
-    if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE || variant == VAR_REGISTER_ROLLED ||
+    if (variant == VAR_REGISTER_PIPE3) {
+        // two batches in flight: FP32 tables, one chunk per warp
+        if (t->elem != ELEM_F32 || chunks != 1) return BLIP_ERR_INVALID_ARG;
+        if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
+    } else if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE || variant == VAR_REGISTER_ROLLED ||
         variant == VAR_REGISTER_L1 || variant == VAR_REGISTER_LOCKSTEP) {
         const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
         if (chunks < 1 || chunks > max_chunks) return BLIP_ERR_INVALID_ARG;
@@ -605,7 +609,7 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
     // sort 2: sorted, and the register kernels' items ordered chunk group
     // slowest
     const bool order_ok = variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE ||
-                          variant == VAR_REGISTER_ROLLED;
+                          variant == VAR_REGISTER_ROLLED || variant == VAR_REGISTER_PIPE3;
     if (sort != 0 && sort != 1 && !(sort == 2 && order_ok)) return BLIP_ERR_INVALID_ARG;
     t->auto_mode = false;
     t->choice = KernelChoice{variant, chunks, warps, sort};
@@ -633,6 +637,10 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
                 cands.push_back(KernelChoice{VAR_REGISTER, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_ROLLED, c, w, srt});
+                if (c == 1 && t->elem == ELEM_F32) {
+                    cands.push_back(KernelChoice{VAR_REGISTER_PIPE3, c, w, srt});
+                    if (srt && t->nchunk > c) cands.push_back(KernelChoice{VAR_REGISTER_PIPE3, c, w, 2});
+                }
                 if (srt && t->nchunk > c) {       // several chunk groups: try their order too
                     cands.push_back(KernelChoice{VAR_REGISTER, c, w, 2});
                     cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, 2});

@@ -9,11 +9,16 @@ cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, 
 {
     if (warps < 1 || warps > 16) return cudaErrorInvalidValue;
     if (variant != VAR_REGISTER && variant != VAR_REGISTER_PIPE && variant != VAR_REGISTER_ROLLED &&
-        variant != VAR_REGISTER_L1 && variant != VAR_REGISTER_LOCKSTEP)
+        variant != VAR_REGISTER_L1 && variant != VAR_REGISTER_LOCKSTEP &&
+        variant != VAR_REGISTER_PIPE3)
+        return cudaErrorInvalidValue;
+    if (variant == VAR_REGISTER_PIPE3 && (elem != ELEM_F32 || chunks != 1))
         return cudaErrorInvalidValue;
     const int pipe = variant == VAR_REGISTER_PIPE ? 1
                    : variant == VAR_REGISTER_ROLLED ? 2
-                   : variant == VAR_REGISTER_L1 ? 3 : variant == VAR_REGISTER_LOCKSTEP ? 4 : 0;
+                   : variant == VAR_REGISTER_L1 ? 3
+                   : variant == VAR_REGISTER_LOCKSTEP ? 4
+                   : variant == VAR_REGISTER_PIPE3 ? 5 : 0;
     switch (elem) {
     case ELEM_F32:
         if (chunks == 1) return launch_register_f32_c1(p, warps, pipe, stream);

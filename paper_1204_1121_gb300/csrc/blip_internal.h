@@ -21,8 +21,9 @@ enum Variant {
     VAR_REGISTER_L1 = 6,      // double-buffered; a block's warps take consecutive
                               // electrons of one chunk group and share rows via L1
     VAR_REGISTER_LOCKSTEP = 7,// as 6, the block's warps in lockstep per row batch
-    VAR_STAGED = 8            // 2 x 2 x TZ cell tiles: union rows staged in shared
+    VAR_STAGED = 8,           // 2 x 2 x TZ cell tiles: union rows staged in shared
                               // memory, every electron of the tile contracted there
+    VAR_REGISTER_PIPE3 = 9    // as 3 with two batches in flight (FP32, 1 chunk per warp)
 };
 
 constexpr int kMaxKpoints = 16;

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 
         __syncwarp();                      // previous item's readers are done with the slice
         float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
-        constexpr bool EARLY = PIPE == 1 || PIPE == 3 || PIPE == 4;   // first loads before the weights
+        constexpr bool EARLY = PIPE == 1 || PIPE == 3 || PIPE == 4 || PIPE == 5;   // first loads before the weights
         const int bad = EARLY ? stencil_geometry_warp<GEO>(p, e, lane, ws, t0, t1, t2, slot)
                               : stencil_setup_warp<GEO>(p, e, lane, ws, slot);
         if (bad && lane == 0 && !dummy) atomicOr(p.status, bad);
@@ -213,30 +213,34 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                 }
                 contract_rows<T, CPW, VEC, VONLY, RB>(ws, (b + 1) * RB, b1, acc);
             }
-        } else if constexpr (PIPE == 1 || PIPE == 3 || PIPE == 4) {
-            // software-pipelined: the next batch of RB rows is in flight while
-            // the current batch is contracted (two register buffers)
+        } else if constexpr (PIPE == 1 || PIPE == 3 || PIPE == 4 || PIPE == 5) {
+            // software-pipelined: the next batch of RB rows (PIPE 5: the next
+            // two batches) is in flight while the current batch is contracted
             constexpr int RB = CPW == 1 ? 8 : (CPW == 2 ? 4 : 2);
             constexpr int NB = 64 / RB;
-            uint4 buf[2][RB][CPW];
+            constexpr int NBUF = PIPE == 5 ? 3 : 2;
+            uint4 buf[NBUF][RB][CPW];
 #pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const char *rp = tbase + (size_t)(ws.colrow[r >> 2] + (r & 3)) * rowb;
+            for (int q = 0; q < NBUF - 1; ++q)
 #pragma unroll
-                for (int c = 0; c < CPW; ++c) buf[0][r][c] = load_row<BLOCKED>(rp + coff[c]);
-            }
+                for (int r = 0; r < RB; ++r) {
+                    const int pt = q * RB + r;
+                    const char *rp = tbase + (size_t)(ws.colrow[pt >> 2] + (pt & 3)) * rowb;
+#pragma unroll
+                    for (int c = 0; c < CPW; ++c) buf[q][r][c] = load_row<BLOCKED>(rp + coff[c]);
+                }
             stencil_weights_warp(p, t0, t1, t2, lane, ws);   // overlaps the first loads
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 if constexpr (PIPE == 4) __syncthreads();
-                if (b + 1 < NB) {
+                if (b + NBUF - 1 < NB) {
 #pragma unroll
                     for (int r = 0; r < RB; ++r) {
-                        const int pt = (b + 1) * RB + r;
+                        const int pt = (b + NBUF - 1) * RB + r;
                         const char *rp = tbase + (size_t)(ws.colrow[pt >> 2] + (pt & 3)) * rowb;
 #pragma unroll
                         for (int c = 0; c < CPW; ++c)
-                            buf[(b + 1) & 1][r][c] = load_row<BLOCKED>(rp + coff[c]);
+                            buf[(b + NBUF - 1) % NBUF][r][c] = load_row<BLOCKED>(rp + coff[c]);
                     }
                 }
 #pragma unroll
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 #pragma unroll
                     for (int c = 0; c < CPW; ++c) {
                         float f[VEC];
-                        Elt<T>::unpack(buf[b & 1][r][c], f);
+                        Elt<T>::unpack(buf[b % NBUF][r][c], f);
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
                             acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
@@ -317,7 +321,11 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 template <typename T, int CPW, bool VONLY, int GEO>
 void launch_pipe(const EvalParams &p, int pipe, dim3 g, dim3 b, size_t smem, cudaStream_t stream)
 {
-    if (pipe == 4) blip_eval_register<T, CPW, VONLY, 4, GEO><<<g, b, smem, stream>>>(p);
+    if (pipe == 5) {
+        // three row buffers only fit the registers for one FP32 chunk
+        if constexpr (std::is_same<T, float>::value && CPW == 1)
+            blip_eval_register<T, CPW, VONLY, 5, GEO><<<g, b, smem, stream>>>(p);
+    } else if (pipe == 4) blip_eval_register<T, CPW, VONLY, 4, GEO><<<g, b, smem, stream>>>(p);
     else if (pipe == 3) blip_eval_register<T, CPW, VONLY, 3, GEO><<<g, b, smem, stream>>>(p);
     else if (pipe == 2) blip_eval_register<T, CPW, VONLY, 2, GEO><<<g, b, smem, stream>>>(p);
     else if (pipe == 1) blip_eval_register<T, CPW, VONLY, 1, GEO><<<g, b, smem, stream>>>(p);
