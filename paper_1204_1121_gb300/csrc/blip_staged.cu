@@ -34,8 +34,10 @@
 //     stage to stage, so the warps of a CTA stay level within a part and
 //     drift across at most two stages (handing the electrons out from a
 //     shared counter instead kept the warps in step at every stage boundary
-//     and was measured about 9 % slower; pairing electrons of one cell to share
-//     row loads gained nothing measurable).
+//     and was measured about 9 % slower).  Units of two electrons - pairs of
+//     one cell sharing each row load, or any two - were measured 0-24 %
+//     slower: the second set of accumulators takes registers that the loads
+//     in flight need.
 // The electrons of a tile are four contiguous slot ranges of the sorted
 // order (one per (a_1, a_2) column of the tile: the brick-major sort key
 // runs along a_3 fastest); positions without a cell sit in the last bucket
