@@ -53,7 +53,8 @@ __device__ __forceinline__ void store_outputs(const EvalParams &p, int e, int gr
 template <typename T, int CPW, int VEC, bool VONLY, int RB>
 __device__ __forceinline__ void contract_rows(const WarpSlice &ws, int pt0,
                                               const uint4 (&buf)[RB][CPW],
-                                              float (&acc)[CPW][VONLY ? 1 : 5][VEC])
+                                              float (&acc)[CPW][VONLY ? 1 : 5][VEC],
+                                              Acc5 (&a5)[CPW][VEC])
 {
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
@@ -65,13 +66,8 @@ __device__ __forceinline__ void contract_rows(const WarpSlice &ws, int pt0,
             Elt<T>::unpack(buf[r][c], f);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
-                if constexpr (!VONLY) {
-                    acc[c][1][v] = fmaf(w.y, f[v], acc[c][1][v]);
-                    acc[c][2][v] = fmaf(w.z, f[v], acc[c][2][v]);
-                    acc[c][3][v] = fmaf(w.w, f[v], acc[c][3][v]);
-                    acc[c][4][v] = fmaf(wl, f[v], acc[c][4][v]);
-                }
+                if constexpr (VONLY) acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
+                else acc5_fma(a5[c][v], w, wl, f[v]);
             }
         }
     }
@@ -147,6 +143,11 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
             for (int k = 0; k < NW; ++k)
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) acc[c][k][v] = 0.0f;
+        Acc5 a5[CPW][VEC];             // five-output accumulators (unused for values only)
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc5_zero(a5[c][v]);
 
         __syncwarp();                      // previous item's readers are done with the slice
         float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
 #pragma unroll
                     for (int c = 0; c < CPW; ++c) b1[r][c] = ldg_stream(rp + coff[c]);
                 }
-                contract_rows<T, CPW, VEC, VONLY, RB>(ws, b * RB, b0, acc);
+                contract_rows<T, CPW, VEC, VONLY, RB>(ws, b * RB, b0, acc, a5);
                 if (b + 2 < NB) {
 #pragma unroll
                     for (int r = 0; r < RB; ++r) {
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                         for (int c = 0; c < CPW; ++c) b0[r][c] = ldg_stream(rp + coff[c]);
                     }
                 }
-                contract_rows<T, CPW, VEC, VONLY, RB>(ws, (b + 1) * RB, b1, acc);
+                contract_rows<T, CPW, VEC, VONLY, RB>(ws, (b + 1) * RB, b1, acc, a5);
             }
         } else if constexpr (PIPE == 1 || PIPE == 3 || PIPE == 4 || PIPE == 5) {
             // software-pipelined: the next batch of RB rows (PIPE 5: the next
@@ -254,13 +255,8 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                         Elt<T>::unpack(buf[b % NBUF][r][c], f);
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
-                            acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
-                            if constexpr (!VONLY) {
-                                acc[c][1][v] = fmaf(w.y, f[v], acc[c][1][v]);
-                                acc[c][2][v] = fmaf(w.z, f[v], acc[c][2][v]);
-                                acc[c][3][v] = fmaf(w.w, f[v], acc[c][3][v]);
-                                acc[c][4][v] = fmaf(wl, f[v], acc[c][4][v]);
-                            }
+                            if constexpr (VONLY) acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
+                            else acc5_fma(a5[c][v], w, wl, f[v]);
                         }
                     }
                 }
@@ -291,17 +287,24 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                             Elt<T>::unpack(raw[cc][kz][c], f);
     #pragma unroll
                             for (int v = 0; v < VEC; ++v) {
-                                acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
-                                if constexpr (!VONLY) {
-                                    acc[c][1][v] = fmaf(w.y, f[v], acc[c][1][v]);
-                                    acc[c][2][v] = fmaf(w.z, f[v], acc[c][2][v]);
-                                    acc[c][3][v] = fmaf(w.w, f[v], acc[c][3][v]);
-                                    acc[c][4][v] = fmaf(wl, f[v], acc[c][4][v]);
-                                }
+                                if constexpr (VONLY) acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
+                                else acc5_fma(a5[c][v], w, wl, f[v]);
                             }
                         }
                     }
             }
+        }
+        if constexpr (!VONLY) {
+#pragma unroll
+            for (int c = 0; c < CPW; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    acc[c][0][v] = a5[c][v].a01.x;
+                    acc[c][1][v] = a5[c][v].a01.y;
+                    acc[c][2][v] = a5[c][v].a23.x;
+                    acc[c][3][v] = a5[c][v].a23.y;
+                    acc[c][4][v] = a5[c][v].a4;
+                }
         }
         if constexpr (PIPE == 4) {
             if (dummy) continue;
