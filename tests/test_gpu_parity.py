@@ -311,7 +311,8 @@ def test_autotune_keeps_results(pb):
     ref = gpu_eval(t, pos)
     dpos = torch.from_numpy(pos).cuda()
     ch = t.autotune(dpos)
-    assert 1 <= ch[0] <= 7 and 1 <= ch[1] <= 8
+    assert 1 <= ch[0] <= 9 and 1 <= ch[1] <= 8 and ch[3] in (0, 1, 2)
+    t.set_kernel(*ch)                  # the chosen configuration is a valid one
     out = gpu_eval(t, pos)
     for a, b in zip(ref, out):
         assert np.array_equal(a, b)
