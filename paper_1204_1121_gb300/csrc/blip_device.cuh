@@ -100,28 +100,50 @@ template <> struct Elt<__half> {
     }
 };
 
-// Accumulators of one stored element's five outputs: value and gradient in
-// packed pairs (value, d/dx) and (d/dy, d/dz), the Laplacian alone.  Each
-// lane of a packed FMA computes the same fma as the scalar form, so results
-// do not change; the FMA instructions per element fall from 5 to 3.
-struct Acc5 {
-    float2 a01, a23;
-    float a4;
+// Accumulators of the five outputs (value, d/dx, d/dy, d/dz, Laplacian) of
+// VEC consecutive stored elements, in packed pairs of neighbouring elements.
+// Each lane of a packed FMA computes the same fma as the scalar form, so the
+// results do not change; the FMA instructions per element halve.
+template <int VEC>
+struct AccPairs {
+    float2 p[5][VEC / 2];
 };
 
-__device__ __forceinline__ void acc5_zero(Acc5 &a)
+template <int VEC>
+__device__ __forceinline__ void pairs_zero(AccPairs<VEC> &a)
 {
-    a.a01 = make_float2(0.0f, 0.0f);
-    a.a23 = make_float2(0.0f, 0.0f);
-    a.a4 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int i = 0; i < VEC / 2; ++i) a.p[k][i] = make_float2(0.0f, 0.0f);
 }
 
-__device__ __forceinline__ void acc5_fma(Acc5 &a, const float4 &w, float wl, float f)
+// a += w_k * f for the five weights of one stencil site.
+template <int VEC>
+__device__ __forceinline__ void pairs_fma(AccPairs<VEC> &a, const float4 &w, float wl,
+                                          const float (&f)[VEC])
 {
-    const float2 ff = make_float2(f, f);
-    a.a01 = __ffma2_rn(make_float2(w.x, w.y), ff, a.a01);
-    a.a23 = __ffma2_rn(make_float2(w.z, w.w), ff, a.a23);
-    a.a4 = fmaf(wl, f, a.a4);
+    const float2 wk[5] = {make_float2(w.x, w.x), make_float2(w.y, w.y), make_float2(w.z, w.z),
+                          make_float2(w.w, w.w), make_float2(wl, wl)};
+#pragma unroll
+    for (int i = 0; i < VEC / 2; ++i) {
+        const float2 ff = make_float2(f[2 * i], f[2 * i + 1]);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a.p[k][i] = __ffma2_rn(wk[k], ff, a.p[k][i]);
+    }
+}
+
+// Unpack into acc[k][v] (k = output, v = element).
+template <int VEC>
+__device__ __forceinline__ void pairs_out(const AccPairs<VEC> &a, float (&acc)[5][VEC])
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int i = 0; i < VEC / 2; ++i) {
+            acc[k][2 * i] = a.p[k][i].x;
+            acc[k][2 * i + 1] = a.p[k][i].y;
+        }
 }
 
 // Per-warp shared-memory slice: 64 x {value, grad x, grad y, grad z} weights,

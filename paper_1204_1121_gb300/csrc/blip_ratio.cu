@@ -60,9 +60,8 @@ __global__ void __launch_bounds__(256) blip_eval_ratio_kernel(EvalParams p, cons
         }
         for (int chunk = 0; chunk < p.nchunk; ++chunk) {
             const size_t coff = ((size_t)chunk * 32 * VEC + (size_t)lane * VEC) * sizeof(T);
-            Acc5 acc[VEC];
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc5_zero(acc[v]);
+            AccPairs<VEC> accp;
+            pairs_zero(accp);
             uint4 buf[2][RB];
 #pragma unroll
             for (int r = 0; r < RB; ++r)
@@ -84,10 +83,11 @@ __global__ void __launch_bounds__(256) blip_eval_ratio_kernel(EvalParams p, cons
                     const float wl = ws.wl[pt];
                     float f[VEC];
                     Elt<T>::unpack(buf[b & 1][r], f);
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc5_fma(acc[v], w, wl, f[v]);
+                    pairs_fma(accp, w, wl, f);
                 }
             }
+            float acc[5][VEC];
+            pairs_out(accp, acc);
             const int l0 = chunk * 32 * VEC + lane * VEC;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
@@ -95,11 +95,9 @@ __global__ void __launch_bounds__(256) blip_eval_ratio_kernel(EvalParams p, cons
                 if (l < p.Lreal) {
                     const float sc = p.scales ? p.scales[l] : 1.0f;
                     const float c = cols[(size_t)e * L + l];
-                    const float a[5] = {acc[v].a01.x, acc[v].a01.y, acc[v].a23.x, acc[v].a23.y,
-                                        acc[v].a4};
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) dot[k] = fmaf(a[k] * sc, c, dot[k]);
-                    if (p.values) __stcs(p.values + (size_t)e * L + l, a[0] * sc);
+                    for (int k = 0; k < 5; ++k) dot[k] = fmaf(acc[k][v] * sc, c, dot[k]);
+                    if (p.values) __stcs(p.values + (size_t)e * L + l, acc[0][v] * sc);
                 }
             }
         }

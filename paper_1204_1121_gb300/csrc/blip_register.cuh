@@ -54,7 +54,7 @@ template <typename T, int CPW, int VEC, bool VONLY, int RB>
 __device__ __forceinline__ void contract_rows(const WarpSlice &ws, int pt0,
                                               const uint4 (&buf)[RB][CPW],
                                               float (&acc)[CPW][VONLY ? 1 : 5][VEC],
-                                              Acc5 (&a5)[CPW][VEC])
+                                              AccPairs<VEC> (&a5)[CPW])
 {
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
@@ -64,10 +64,11 @@ __device__ __forceinline__ void contract_rows(const WarpSlice &ws, int pt0,
         for (int c = 0; c < CPW; ++c) {
             float f[VEC];
             Elt<T>::unpack(buf[r][c], f);
+            if constexpr (VONLY) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                if constexpr (VONLY) acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
-                else acc5_fma(a5[c][v], w, wl, f[v]);
+                for (int v = 0; v < VEC; ++v) acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
+            } else {
+                pairs_fma(a5[c], w, wl, f);
             }
         }
     }
@@ -143,11 +144,9 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
             for (int k = 0; k < NW; ++k)
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) acc[c][k][v] = 0.0f;
-        Acc5 a5[CPW][VEC];             // five-output accumulators (unused for values only)
+        AccPairs<VEC> a5[CPW];         // five-output accumulators (unused for values only)
 #pragma unroll
-        for (int c = 0; c < CPW; ++c)
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc5_zero(a5[c][v]);
+        for (int c = 0; c < CPW; ++c) pairs_zero(a5[c]);
 
         __syncwarp();                      // previous item's readers are done with the slice
         float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
@@ -253,10 +252,11 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                     for (int c = 0; c < CPW; ++c) {
                         float f[VEC];
                         Elt<T>::unpack(buf[b % NBUF][r][c], f);
+                        if constexpr (VONLY) {
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            if constexpr (VONLY) acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
-                            else acc5_fma(a5[c][v], w, wl, f[v]);
+                            for (int v = 0; v < VEC; ++v) acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
+                        } else {
+                            pairs_fma(a5[c], w, wl, f);
                         }
                     }
                 }
@@ -285,10 +285,12 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
                         for (int c = 0; c < CPW; ++c) {
                             float f[VEC];
                             Elt<T>::unpack(raw[cc][kz][c], f);
-    #pragma unroll
-                            for (int v = 0; v < VEC; ++v) {
-                                if constexpr (VONLY) acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
-                                else acc5_fma(a5[c][v], w, wl, f[v]);
+                                if constexpr (VONLY) {
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v)
+                                    acc[c][0][v] = fmaf(w.x, f[v], acc[c][0][v]);
+                            } else {
+                                pairs_fma(a5[c], w, wl, f);
                             }
                         }
                     }
@@ -296,15 +298,7 @@ __global__ void __launch_bounds__(512) blip_eval_register(EvalParams p)
         }
         if constexpr (!VONLY) {
 #pragma unroll
-            for (int c = 0; c < CPW; ++c)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    acc[c][0][v] = a5[c][v].a01.x;
-                    acc[c][1][v] = a5[c][v].a01.y;
-                    acc[c][2][v] = a5[c][v].a23.x;
-                    acc[c][3][v] = a5[c][v].a23.y;
-                    acc[c][4][v] = a5[c][v].a4;
-                }
+            for (int c = 0; c < CPW; ++c) pairs_out(a5[c], acc[c]);
         }
         if constexpr (PIPE == 4) {
             if (dummy) continue;
