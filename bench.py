@@ -459,6 +459,9 @@ def main():
         # one electron per launch (particle-by-particle order), 1,536 kernel
         # nodes in one CUDA graph
         o1 = t.alloc_outputs(E)
+        one_choice = list(chosen)
+        if args.kernel == "auto":      # tune the one-electron launch too
+            one_choice = list(t.autotune(dpos[:1].contiguous(), out=tuple(x[:1] for x in o1)))
         g = t.graph(dpos, o1, 1)
         for _ in range(2):
             g.launch()
@@ -473,7 +476,8 @@ def main():
         oms = a.elapsed_time(b) / reps
         line["one_at_a_time"] = {"value": evals / (oms / 1e3), "ms_per_step": oms,
                                  "us_per_electron": 1e3 * oms / E,
-                                 "how": "CUDA graph of 1,536 single-electron launches"}
+                                 "how": "CUDA graph of 1,536 single-electron launches",
+                                 "kernel_choice": one_choice}
         g.close()
 
     if w.is_complex:

@@ -277,6 +277,9 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
         if (rc) return rc;
         CK(launch_staged(p, t->elem, kc.chunks, kc.warps, cell_end, *tm, t->sm_count, t->test_stall,
                          stream));
+    } else if (kc.variant == VAR_SPLIT) {
+        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
+        CK(launch_split(p, t->elem, stream));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
     }
@@ -580,7 +583,10 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         t->auto_mode = true;
         return BLIP_OK;
     }
-    if (variant == VAR_REGISTER_PIPE3) {
+    if (variant == VAR_SPLIT) {
+        // one chunk per item, 4 warps per block; no Bloch epilogue
+        if (t->n_k || chunks != 1 || warps != 4) return BLIP_ERR_INVALID_ARG;
+    } else if (variant == VAR_REGISTER_PIPE3) {
         // two batches in flight: FP32 tables, one chunk per warp
         if (t->elem != ELEM_F32 || chunks != 1) return BLIP_ERR_INVALID_ARG;
         if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
@@ -656,6 +662,7 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
         if (srt)
             for (int g : {2, 4})
                 for (int w : {4, 8}) cands.push_back(KernelChoice{VAR_GROUPED, g, w, 1});
+        if (!t->n_k) cands.push_back(KernelChoice{VAR_SPLIT, 1, 4, srt});
         if (srt && !t->n_k)
             for (int tz : {2, 4})
                 for (int cw : {12, 16}) cands.push_back(KernelChoice{VAR_STAGED, tz, cw, 1});
@@ -741,7 +748,7 @@ int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koff
     for (int q = 0; q <= n_k; ++q) t->koff[q] = koffs[q];
     t->n_k = n_k;
     auto has_bloch = [](const KernelChoice &kc) {
-        return kc.variant != VAR_BULK && kc.variant != VAR_STAGED;
+        return kc.variant != VAR_BULK && kc.variant != VAR_STAGED && kc.variant != VAR_SPLIT;
     };
     if (!has_bloch(t->choice)) t->choice = KernelChoice{VAR_REGISTER, 1, 8, 0};
     for (auto &kv : t->tuned)
@@ -952,6 +959,9 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
         if (rc) return rc;
         CK(launch_staged(p, t->elem, kc.chunks, kc.warps, cell_end, *tm, t->sm_count, t->test_stall,
                          s));
+    } else if (kc.variant == VAR_SPLIT) {
+        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
+        CK(launch_split(p, t->elem, s));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, s));
     }

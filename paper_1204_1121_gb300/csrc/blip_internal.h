@@ -23,7 +23,9 @@ enum Variant {
     VAR_REGISTER_LOCKSTEP = 7,// as 6, the block's warps in lockstep per row batch
     VAR_STAGED = 8,           // 2 x 2 x TZ cell tiles: union rows staged in shared
                               // memory, every electron of the tile contracted there
-    VAR_REGISTER_PIPE3 = 9    // as 3 with two batches in flight (FP32, 1 chunk per warp)
+    VAR_REGISTER_PIPE3 = 9,   // as 3 with two batches in flight (FP32, 1 chunk per warp)
+    VAR_SPLIT = 10            // 4 warps per (electron, chunk), one a_1 slab of the
+                              // stencil each: one round of latency (small launches)
 };
 
 constexpr int kMaxKpoints = 16;
@@ -143,6 +145,11 @@ cudaError_t make_staged_tmap(const void *table, int elem, long long row_stride, 
 // and tz.  stall != 0 is the same test hook as for launch_bulk.
 cudaError_t launch_staged(const EvalParams &p, int elem, int tz, int cw, const int *cell_end,
                           const TmaDesc &tmap, int sm_count, int stall, cudaStream_t stream);
+
+// Launch the split-stencil kernel: a block of 4 warps per (electron, chunk),
+// warp q contracting the 16 sites of a_1 slab q, partial sums added in a
+// fixed order (p.groups must equal p.nchunk).
+cudaError_t launch_split(const EvalParams &p, int elem, cudaStream_t stream);
 
 // Sherman-Morrison update of n_walkers inverses after one accepted move each
 // (blip_sm.cu); work holds [n_walkers][2 n] floats.

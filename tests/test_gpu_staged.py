@@ -89,7 +89,9 @@ def test_staged_matches_register_kernel_and_oracle(pb, grid, n_orb, storage):
         t.status()
     bad = ~np.isfinite(pos).all(1)
     assert np.isnan(ref[0][bad]).all() and np.isnan(ref[1][bad]).all()
-    good = ~bad
+    # the far position (|u| > 2^40, flagged) keeps only a few fractional bits,
+    # so its value depends on the last bits of A^-1: checked for the flag only
+    good = ~bad & (np.abs(pos).max(1) < 1e9)
     compare(grid, lat, tab, pos[good], [r[good] for r in ref], storage=kind,
             scales=None if kind == pb.F32 or cplx else _scales(tab),
             sample=np.random.default_rng(5).choice(good.sum(), 300, replace=False))
