@@ -33,14 +33,16 @@ import blip_inputs as bi  # noqa: E402
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the evaluation kernel on this workload, from ncu, keyed by the SHA-256 of
-# the kernel source it was measured on; reported as null once the kernel
-# changes.  Filled from the committed summary under profiles/.
+# the kernel sources it was measured on and by the kernel (variant, chunks);
+# reported as null once the sources change.  Filled from the committed
+# summaries under profiles/.
 NCU_TRAFFIC = {
-    # (kernel source hash, workload, storage, electrons): (variant, chunks, bytes)
-    ("a9dfaac619ec933e", "tio2", "f32", 1536): (9, 1, 275688192 + 13026048),
+    # (kernel source hash, workload, storage, electrons): {(variant, chunks): bytes}
+    ("ef85fc96233ef064", "tio2", "f32", 1536): {(9, 1): 275612160 + 12713728,
+                                                (3, 2): 274916864 + 11676928},
     # captured with 128 orbitals, scaled x6 to 768 (rows and outputs grow
     # in proportion to the orbital count)
-    ("a9dfaac619ec933e", "tio2_batch", "f32", 393216): (8, 4, 6 * (156547328 + 947058688)),
+    ("ef85fc96233ef064", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156529408 + 948103936)},
 }
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "c64": 3, "bf16pair": 4}
@@ -397,8 +399,7 @@ def main():
     bytes_alg = U * Lr * ELEM_BYTES[args.storage] + 20 * Lr * E + 24 * E
     peak, peak_kind = measured_peaks()
     kh = kernel_hash()
-    rec = NCU_TRAFFIC.get((kh, w.name, args.storage, E))
-    rec = rec[2] if rec and tuple(rec[:2]) == tuple(chosen[:2]) else None
+    rec = NCU_TRAFFIC.get((kh, w.name, args.storage, E), {}).get(tuple(chosen[:2]))
     # FP32 FMA peak from unit counts and clock: SMs x 128 FP32 lanes x 2 FLOP
     # x 2.07 GHz (maximum SM clock)
     sms = info["sm_count"]
