@@ -6,9 +6,18 @@
 // With Dinv[l][k] = (D^{-1})_{lk} and w_k = sum_l psi'_l Dinv[l][k]
 // (w_j = xi, the acceptance ratio),
 //     Dinv'[l][k] = Dinv[l][k] - Dinv[l][j] (w_k - delta_jk) / w_j.
-// Two HBM-bound passes per walker: a GEMV for w (reads Dinv once; also keeps
-// column j aside) and the rank-1 update (reads and writes Dinv once), i.e.
-// 12 n^2 bytes per walker update in FP32.
+// For n <= 1024 (the TiO2 cell's 768 electrons of one spin) the update is
+// one read and one write of Dinv, 8 n^2 bytes per walker in FP32:
+//   1. sm_column_kernel, one warp per walker: column j of Dinv and
+//      w_j = sum_l psi'_l Dinv[l][j] (the ratio), kept aside;
+//   2. sm_fused_kernel, one block per (walker, 32 columns): 32 warps hold
+//      the block's n x 32 slice of Dinv in registers (ceil(n / 32) rows each,
+//      a lane per column), form w_k for their columns (partial sums over the
+//      warps added in a fixed order), then update the slice in registers and
+//      write it back.
+// Larger n takes two passes: a GEMV for w (reads Dinv once; also keeps
+// column j aside) and the rank-1 update (reads and writes Dinv once), 12 n^2
+// bytes per walker.
 #include <cuda_runtime.h>
 
 #include "blip_internal.h"
@@ -80,11 +89,104 @@ __global__ void __launch_bounds__(SM_THREADS) sm_rank1_kernel(int n, float *__re
     }
 }
 
+constexpr int FU_WARPS = 32;                 // warps per fused block
+constexpr int FU_MAX_ROWS = 32;              // rows per warp: n <= 1024
+
+// work[wk][n + l] = Dinv[l][j]; work[wk][j] = w_j = sum_l psi'_l Dinv[l][j].
+__global__ void __launch_bounds__(32) sm_column_kernel(int n, const float *__restrict__ dinv,
+                                                       const float *__restrict__ rows,
+                                                       const int *__restrict__ cols,
+                                                       float *__restrict__ work)
+{
+    const int wk = blockIdx.x;
+    const int j = cols[wk];
+    if (j < 0 || j >= n) return;
+    const float *D = dinv + (size_t)wk * n * n;
+    const float *r = rows + (size_t)wk * n;
+    float *w = work + (size_t)wk * 2 * n;
+    const int lane = threadIdx.x;
+    float acc = 0.0f;
+    for (int l = lane; l < n; l += 32) {
+        const float d = D[(size_t)l * n + j];
+        w[n + l] = d;
+        acc = fmaf(__ldg(r + l), d, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) w[j] = acc;
+}
+
+// One block per (walker, 32 columns): the slice stays in registers between
+// the product w_k = sum_l psi'_l Dinv[l][k] and the update
+// Dinv[l][k] -= Dinv[l][j] (w_k - delta_jk) / w_j.
+template <int RPW>
+__global__ void __launch_bounds__(32 * FU_WARPS) sm_fused_kernel(int n, float *__restrict__ dinv,
+                                                                 const float *__restrict__ rows,
+                                                                 const int *__restrict__ cols,
+                                                                 const float *__restrict__ work)
+{
+    __shared__ float part[FU_WARPS][32];
+    const int wk = blockIdx.y;
+    const int j = cols[wk];
+    if (j < 0 || j >= n) return;                       // no accepted move: unchanged
+    float *D = dinv + (size_t)wk * n * n;
+    const float *r = rows + (size_t)wk * n;
+    const float *w = work + (size_t)wk * 2 * n;
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
+    const bool kin = k < n;
+    const int l0 = q * RPW;
+    const int nr = max(0, min(RPW, n - l0));             // rows of this warp
+    float d[RPW];
+    float acc = 0.0f;
+    {
+        const float *pd = D + (size_t)l0 * n + (kin ? k : 0);
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            d[i] = (kin && i < nr) ? *pd : 0.0f;
+            if (i < nr) acc = fmaf(__ldg(r + l0 + i), d[i], acc);
+            pd += n;
+        }
+    }
+    part[q][lane] = acc;
+    __syncthreads();
+    float wk_ = 0.0f;
+#pragma unroll
+    for (int p = 0; p < FU_WARPS; ++p) wk_ += part[p][lane];
+    const float f = (wk_ - (k == j ? 1.0f : 0.0f)) / w[j];
+    if (kin) {
+        float *pd = D + (size_t)l0 * n + k;
+        const float *cj = w + n + l0;
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            if (i < nr) *pd = fmaf(-cj[i], f, d[i]);
+            pd += n;
+        }
+    }
+}
+
+template <int RPW>
+void launch_fused(int n_walkers, int n, float *dinv, const float *rows, const int *cols,
+                  float *work, cudaStream_t stream)
+{
+    sm_column_kernel<<<n_walkers, 32, 0, stream>>>(n, dinv, rows, cols, work);
+    const dim3 g((n + 31) / 32, n_walkers);
+    sm_fused_kernel<RPW><<<g, 32 * FU_WARPS, 0, stream>>>(n, dinv, rows, cols, work);
+}
+
 }  // namespace
 
 cudaError_t launch_sm_update(int n_walkers, int n, float *dinv, const float *rows, const int *cols,
                              float *work, cudaStream_t stream)
 {
+    const int rpw = (n + FU_WARPS - 1) / FU_WARPS;
+    if (rpw <= FU_MAX_ROWS) {
+        if (rpw <= 8) launch_fused<8>(n_walkers, n, dinv, rows, cols, work, stream);
+        else if (rpw <= 16) launch_fused<16>(n_walkers, n, dinv, rows, cols, work, stream);
+        else if (rpw <= 24) launch_fused<24>(n_walkers, n, dinv, rows, cols, work, stream);
+        else launch_fused<FU_MAX_ROWS>(n_walkers, n, dinv, rows, cols, work, stream);
+        return cudaGetLastError();
+    }
     const dim3 g1((n + 31) / 32, n_walkers);
     sm_gemv_kernel<<<g1, 32 * SM_PARTS, 0, stream>>>(n, dinv, rows, cols, work);
     const dim3 g2((n + SM_THREADS - 1) / SM_THREADS, (n + SM_ROWS - 1) / SM_ROWS, n_walkers);

@@ -19,7 +19,7 @@ def pb():
     return pb
 
 
-@pytest.mark.parametrize("n", [1, 5, 96, 257, 768])
+@pytest.mark.parametrize("n", [1, 5, 33, 96, 257, 768, 1024, 1100])
 def test_sm_update_matches_oracle(pb, n):
     rng = np.random.default_rng(n)
     W = 5
