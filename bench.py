@@ -33,16 +33,18 @@ import blip_inputs as bi  # noqa: E402
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the evaluation kernel on this workload, from ncu, keyed by the SHA-256 of
-# the kernel sources it was measured on and by the kernel (variant, chunks);
-# reported as null once the sources change.  Filled from the committed
-# summaries under profiles/.
+# the evaluation-path sources it was measured on (kernel_hash) and by the
+# kernel (variant, chunks); reported as null once those sources change.
+# Filled from the committed summaries under profiles/ (the summaries give
+# the hash of all library sources at capture time, ef85fc96233ef064; the
+# evaluation-path sources are unchanged since).
 NCU_TRAFFIC = {
     # (kernel source hash, workload, storage, electrons): {(variant, chunks): bytes}
-    ("ef85fc96233ef064", "tio2", "f32", 1536): {(9, 1): 275612160 + 12713728,
+    ("e4c0ab6b52dbb9b0", "tio2", "f32", 1536): {(9, 1): 275612160 + 12713728,
                                                 (3, 2): 274916864 + 11676928},
     # captured with 128 orbitals, scaled x6 to 768 (rows and outputs grow
     # in proportion to the orbital count)
-    ("ef85fc96233ef064", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156529408 + 948103936)},
+    ("e4c0ab6b52dbb9b0", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156529408 + 948103936)},
 }
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "c64": 3, "bf16pair": 4}
@@ -117,11 +119,12 @@ def touched_sites(grid, lattice, pos):
 
 
 def kernel_hash():
-    """SHA-256 (16 hex digits) of every CUDA source of the library."""
+    """SHA-256 (16 hex digits) of every CUDA source of the evaluation path
+    (all of the library but the Sherman-Morrison update)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1204_1121_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")) and f != "blip_sm.cu":
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
