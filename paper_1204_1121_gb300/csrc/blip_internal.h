@@ -39,6 +39,28 @@ struct Geometry {
     float norm;        // 1, or (3/2)^3 for phi(0) = 1 blips
 };
 
+// Spatial sort key of grid cell (x, y, z): 8 x 8 bricks of whole a_3
+// columns, grouped 4 x 4 into super-bricks of 32 x 32 columns; super-bricks
+// in row-major order, bricks inside a super-brick row-major, columns inside
+// a brick row-major, a_3 fastest.  A brick's neighbour along a_1 then comes 4
+// bricks later in the order (not a whole row of bricks later), so most of
+// the halo rows their stencils share are still in L2 when the second brick
+// reads them.
+__host__ __device__ inline int sort_cell_key(const Geometry &g, int x, int y, int z)
+{
+    const int nsy = (g.n[1] + 31) >> 5;                      // super-bricks along a_2
+    const int sb = (x >> 5) * nsy + (y >> 5);
+    const int br = ((x >> 3) & 3) * 4 + ((y >> 3) & 3);
+    const int col = (x & 7) * 8 + (y & 7);
+    return ((sb * 16 + br) * 64 + col) * g.n[2] + z;
+}
+
+// Number of cell keys (the key of positions without a cell is this number).
+__host__ __device__ inline long long sort_key_count(const Geometry &g)
+{
+    return (long long)((g.n[0] + 31) >> 5) * ((g.n[1] + 31) >> 5) * 1024 * g.n[2];
+}
+
 // Per-electron geometry computed once by the sort pre-pass (FP64 wrap done
 // there): base cell, FP32 offsets and status bits, stored in slot order.
 struct __align__(16) ElecGeo {

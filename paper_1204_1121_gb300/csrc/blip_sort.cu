@@ -5,13 +5,15 @@
 // (Sec. IV.A, Eq. 11.12.23.1) into cache-friendly work; the paper itself
 // evaluates in input order.
 //
-// The order is brick-major: the (a_1, a_2) plane is cut into 8 x 8 bricks of
-// whole z-columns, bricks in row-major order, and inside a brick the cells in
-// row-major order with z fastest (the table's own row order).  A window of
-// consecutively evaluated electrons then covers a compact 3-D region, so the
-// rows its stencils share along a_1 and a_2 are still in L2 when reused;
-// with a plain row-major cell order the a_1 neighbours come one whole
-// (a_2, a_3) plane later.
+// The order is brick-major (sort_cell_key): the (a_1, a_2) plane is cut into
+// 8 x 8 bricks of whole z-columns, grouped 4 x 4 into super-bricks; super-
+// bricks and the bricks inside them in row-major order, and inside a brick
+// the cells in row-major order with z fastest (the table's own row order).
+// A window of consecutively evaluated electrons then covers a compact 3-D
+// region, so the rows its stencils share along a_1 and a_2 are still in L2
+// when reused; with a plain row-major cell order the a_1 neighbours come one
+// whole (a_2, a_3) plane later, and with row-major bricks alone a whole row
+// of bricks later.
 //
 // Counting sort over these cell keys (plus one bucket for positions without
 // a cell), in four kernels:
@@ -70,10 +72,7 @@ __global__ void sort_keys_kernel(Geometry geo, const double *__restrict__ pos, i
             r.pad = 0.0f;
             rec[e] = r;
         }
-        const int nby = (geo.n[1] + 7) >> 3;
-        const int key = ok ? ((((idx[0] >> 3) * nby + (idx[1] >> 3)) * 8 + (idx[0] & 7)) * 8
-                              + (idx[1] & 7)) * geo.n[2] + idx[2]
-                           : P;
+        const int key = ok ? sort_cell_key(geo, idx[0], idx[1], idx[2]) : P;
         keys[e] = key;
         atomicAdd(hist + key, 1);
     }
@@ -141,12 +140,9 @@ __global__ void sort_scatter_kernel(const int *__restrict__ keys, int n_elec,
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Cell keys: whole 8 x 8 bricks of z-columns, so the key range covers the
-// grid rounded up to multiples of 8 along a_1 and a_2.
-long long sort_buckets(const Geometry &geo)
-{
-    return (long long)((geo.n[0] + 7) / 8 * 8) * ((geo.n[1] + 7) / 8 * 8) * geo.n[2];
-}
+// Cell keys (sort_cell_key): whole 32 x 32 super-bricks of z-columns, so the
+// key range covers the grid rounded up to multiples of 32 along a_1 and a_2.
+long long sort_buckets(const Geometry &geo) { return sort_key_count(geo); }
 
 }  // namespace
 

@@ -82,7 +82,6 @@ struct StagedArgs {
     const int *cell_end;   // sort: one past the last slot of each key
     int nty, ntz;          // tiles along a_2, a_3
     int ntiles;
-    int nby;               // 8-cell bricks along a_2 (sort key)
     int P;                 // key of positions without a cell
     int stall;             // test hook: consumers never release the first stage
 };
@@ -103,12 +102,6 @@ __device__ __forceinline__ void prefetch_l2(const void *src, unsigned size)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(size) : "memory");
 }
 
-// Sort key of cell (x, y, z): 8 x 8 bricks of whole a_3 columns, bricks in
-// row-major order, cells inside a brick row-major with a_3 fastest.
-__device__ __forceinline__ int cell_key(const Geometry &g, int nby, int x, int y, int z)
-{
-    return ((((x >> 3) * nby + (y >> 3)) * 8 + (x & 7)) * 8 + (y & 7)) * g.n[2] + z;
-}
 
 struct TileInfo {
     int x0, y0, z0, nz;
@@ -134,7 +127,7 @@ __device__ __forceinline__ void tile_info(const EvalParams &p, const StagedArgs 
         const int x = ti.x0 + c / kTY, y = ti.y0 + c % kTY;
         int s = 0, e = 0;
         if (x < p.geo.n[0] && y < p.geo.n[1]) {
-            const int k0 = cell_key(p.geo, a.nby, x, y, ti.z0);
+            const int k0 = sort_cell_key(p.geo, x, y, ti.z0);     // a_3 runs are consecutive keys
             s = k0 ? a.cell_end[k0 - 1] : 0;
             e = a.cell_end[k0 + ti.nz - 1];
         }
@@ -508,8 +501,7 @@ cudaError_t launch_staged(const EvalParams &p, int elem, int tz, int cw, const i
     StagedArgs a{};
     a.cell_end = cell_end;
     a.nty = (p.geo.n[1] + kTY - 1) / kTY;
-    a.nby = (p.geo.n[1] + 7) >> 3;
-    a.P = ((p.geo.n[0] + 7) / 8 * 8) * ((p.geo.n[1] + 7) / 8 * 8) * p.geo.n[2];
+    a.P = (int)sort_key_count(p.geo);
     a.stall = stall;
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(&tmap);
     switch (elem) {
