@@ -10,9 +10,10 @@
 // one read and one write of Dinv, 8 n^2 bytes per walker in FP32:
 //   1. sm_column_kernel, one warp per walker: column j of Dinv and
 //      w_j = sum_l psi'_l Dinv[l][j] (the ratio), kept aside;
-//   2. sm_fused_kernel, one block per (walker, 32 columns): 32 warps hold
-//      the block's n x 32 slice of Dinv in registers (ceil(n / 32) rows each,
-//      a lane per column), form w_k for their columns (partial sums over the
+//   2. sm_fused_kernel, one block per (walker, 32 columns): 16 warps hold
+//      the block's n x 32 slice of Dinv in registers (ceil(n / 16) rows each,
+//      a lane per column; two blocks fit an SM, so one block's loads overlap
+//      the other's stores), form w_k for their columns (partial sums over the
 //      warps added in a fixed order), then update the slice in registers and
 //      write it back.
 // Larger n takes two passes: a GEMV for w (reads Dinv once; also keeps
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(SM_THREADS) sm_rank1_kernel(int n, float *__re
     }
 }
 
-constexpr int FU_WARPS = 32;                 // warps per fused block
-constexpr int FU_MAX_ROWS = 32;              // rows per warp: n <= 1024
+constexpr int FU_WARPS = 16;                 // warps per fused block
+constexpr int FU_MAX_ROWS = 64;              // rows per warp: n <= 1024
 
 // work[wk][n + l] = Dinv[l][j]; work[wk][j] = w_j = sum_l psi'_l Dinv[l][j].
 __global__ void __launch_bounds__(32) sm_column_kernel(int n, const float *__restrict__ dinv,
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(32) sm_column_kernel(int n, const float *__res
 // the product w_k = sum_l psi'_l Dinv[l][k] and the update
 // Dinv[l][k] -= Dinv[l][j] (w_k - delta_jk) / w_j.
 template <int RPW>
-__global__ void __launch_bounds__(32 * FU_WARPS) sm_fused_kernel(int n, float *__restrict__ dinv,
+__global__ void __launch_bounds__(32 * FU_WARPS, 2) sm_fused_kernel(int n, float *__restrict__ dinv,
                                                                  const float *__restrict__ rows,
                                                                  const int *__restrict__ cols,
                                                                  const float *__restrict__ work)
@@ -181,9 +182,9 @@ cudaError_t launch_sm_update(int n_walkers, int n, float *dinv, const float *row
 {
     const int rpw = (n + FU_WARPS - 1) / FU_WARPS;
     if (rpw <= FU_MAX_ROWS) {
-        if (rpw <= 8) launch_fused<8>(n_walkers, n, dinv, rows, cols, work, stream);
-        else if (rpw <= 16) launch_fused<16>(n_walkers, n, dinv, rows, cols, work, stream);
-        else if (rpw <= 24) launch_fused<24>(n_walkers, n, dinv, rows, cols, work, stream);
+        if (rpw <= 16) launch_fused<16>(n_walkers, n, dinv, rows, cols, work, stream);
+        else if (rpw <= 32) launch_fused<32>(n_walkers, n, dinv, rows, cols, work, stream);
+        else if (rpw <= 48) launch_fused<48>(n_walkers, n, dinv, rows, cols, work, stream);
         else launch_fused<FU_MAX_ROWS>(n_walkers, n, dinv, rows, cols, work, stream);
         return cudaGetLastError();
     }
