@@ -221,26 +221,86 @@ int staged_tmap(blip_table_s *t, int tz, const TmaDesc **out)
     return BLIP_OK;
 }
 
-int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs, int n_walkers,
-                void *values, void *grads, void *laps, cudaStream_t stream, const KernelChoice &kc)
+// The bulk-copy, staged-tile and split-stencil kernels have no Bloch epilogue.
+bool has_bloch_epilogue(const KernelChoice &kc)
 {
-    if (n_elec == 0) return BLIP_OK;
+    return kc.variant != VAR_BULK && kc.variant != VAR_STAGED && kc.variant != VAR_SPLIT;
+}
+
+// Launch parameters of an evaluation with kernel choice kc; the evaluation
+// order (perm, georec) is left to the caller.
+EvalParams make_params(const blip_table_s *t, const double *pos, int n_elec, const int *offs,
+                       int n_walkers, void *values, void *grads, void *laps,
+                       const KernelChoice &kc)
+{
     EvalParams p{};
     p.table = t->d_table;
     p.scales = t->d_scales;
     p.row_stride = t->row_stride;
     p.Lreal = t->Lreal;
     p.nchunk = t->nchunk;
-    const bool grouped = kc.variant == VAR_GROUPED;
-    const bool staged = kc.variant == VAR_STAGED;
-    p.groups = (grouped || staged) ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
+    const bool per_chunk = kc.variant == VAR_GROUPED || kc.variant == VAR_STAGED;
+    p.groups = per_chunk ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
     p.items = (long long)n_elec * p.groups;
     p.geo = t->geo;
     p.pos = pos;
     p.n_elec = n_elec;
     p.perm = nullptr;
-    if (staged && t->n_k) return BLIP_ERR_INVALID_ARG;    // no Bloch epilogue in this kernel
-    if (kc.sort || grouped || staged) {
+    p.georec = nullptr;
+    p.group_major = kc.sort == 2 ? 1 : 0;
+    p.offsets = offs;
+    p.n_walkers = offs ? n_walkers : 0;
+    p.values = static_cast<float *>(values);
+    p.grads = static_cast<float *>(grads);
+    p.laps = static_cast<float *>(laps);
+    p.vec_out = (t->Lreal % 4 == 0) && aligned16(values) &&
+                (!grads || (aligned16(grads) && aligned16(laps)));
+    p.status = t->d_status;
+    copy_kpoints(t, p);
+    return p;
+}
+
+// Launch kernel choice kc on prepared parameters; scratch holds the sort
+// whose views the grouped and staged kernels read.
+int launch_choice(blip_table_s *t, const EvalParams &p, const KernelChoice &kc, void *scratch,
+                  cudaStream_t stream)
+{
+    if (t->n_k && !has_bloch_epilogue(kc)) return BLIP_ERR_INVALID_ARG;
+    if (kc.variant == VAR_BULK) {
+        const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
+        int per_sm = (int)((228 * 1024) / (smem + 1024));
+        per_sm = std::max(1, std::min(per_sm, 4));
+        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, t->test_stall,
+                       stream));
+    } else if (kc.variant == VAR_GROUPED) {
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, p.n_elec, scratch, &keys, &cell_end);
+        CK(launch_grouped(p, t->elem, kc.chunks, kc.warps, keys, cell_end, stream));
+    } else if (kc.variant == VAR_STAGED) {
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, p.n_elec, scratch, &keys, &cell_end);
+        const TmaDesc *tm = nullptr;
+        int rc = staged_tmap(t, kc.chunks, &tm);
+        if (rc) return rc;
+        CK(launch_staged(p, t->elem, kc.chunks, kc.warps, cell_end, *tm, t->sm_count, t->test_stall,
+                         stream));
+    } else if (kc.variant == VAR_SPLIT) {
+        CK(launch_split(p, t->elem, stream));
+    } else {
+        CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
+    }
+    t->last_stream = stream;
+    t->used = true;
+    return BLIP_OK;
+}
+
+int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs, int n_walkers,
+                void *values, void *grads, void *laps, cudaStream_t stream, const KernelChoice &kc)
+{
+    if (n_elec == 0) return BLIP_OK;
+    if (t->n_k && !has_bloch_epilogue(kc)) return BLIP_ERR_INVALID_ARG;
+    EvalParams p = make_params(t, pos, n_elec, offs, n_walkers, values, grads, laps, kc);
+    if (kc.sort || kc.variant == VAR_GROUPED || kc.variant == VAR_STAGED) {
         int *perm = nullptr;
         const ElecGeo *rec = nullptr;
         const bool want_rec = t->n_k == 0 && kc.variant != VAR_BULK;
@@ -249,43 +309,7 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
         p.perm = perm;
         p.georec = rec;
     }
-    p.group_major = kc.sort == 2 ? 1 : 0;
-    p.offsets = offs;
-    p.n_walkers = offs ? n_walkers : 0;
-    p.values = static_cast<float *>(values);
-    p.grads = static_cast<float *>(grads);
-    p.laps = static_cast<float *>(laps);
-    p.vec_out = (t->Lreal % 4 == 0) && aligned16(values) && (!grads || (aligned16(grads) && aligned16(laps)));
-    p.status = t->d_status;
-    copy_kpoints(t, p);
-    if (kc.variant == VAR_BULK) {
-        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
-        const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
-        int per_sm = (int)((228 * 1024) / (smem + 1024));
-        per_sm = std::max(1, std::min(per_sm, 4));
-        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, t->test_stall,
-                       stream));
-    } else if (grouped) {
-        const int *keys = nullptr, *cell_end = nullptr;
-        sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
-        CK(launch_grouped(p, t->elem, kc.chunks, kc.warps, keys, cell_end, stream));
-    } else if (staged) {
-        const int *keys = nullptr, *cell_end = nullptr;
-        sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
-        const TmaDesc *tm = nullptr;
-        int rc = staged_tmap(t, kc.chunks, &tm);
-        if (rc) return rc;
-        CK(launch_staged(p, t->elem, kc.chunks, kc.warps, cell_end, *tm, t->sm_count, t->test_stall,
-                         stream));
-    } else if (kc.variant == VAR_SPLIT) {
-        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
-        CK(launch_split(p, t->elem, stream));
-    } else {
-        CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
-    }
-    t->last_stream = stream;
-    t->used = true;
-    return BLIP_OK;
+    return launch_choice(t, p, kc, t->scratch, stream);
 }
 
 int grow_stage(blip_table_s *t, size_t bytes)
@@ -761,12 +785,9 @@ int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koff
         }
     for (int q = 0; q <= n_k; ++q) t->koff[q] = koffs[q];
     t->n_k = n_k;
-    auto has_bloch = [](const KernelChoice &kc) {
-        return kc.variant != VAR_BULK && kc.variant != VAR_STAGED && kc.variant != VAR_SPLIT;
-    };
-    if (!has_bloch(t->choice)) t->choice = KernelChoice{VAR_REGISTER, 1, 8, 0};
+    if (!has_bloch_epilogue(t->choice)) t->choice = KernelChoice{VAR_REGISTER, 1, 8, 0};
     for (auto &kv : t->tuned)
-        if (!has_bloch(kv.second)) kv.second = KernelChoice{VAR_REGISTER, 1, 8, 0};
+        if (!has_bloch_epilogue(kv.second)) kv.second = KernelChoice{VAR_REGISTER, 1, 8, 0};
     return BLIP_OK;
 }
 
@@ -926,60 +947,13 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
     rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the sort clears its histogram itself and overwrites everything else it reads
+    const KernelChoice kc = pick(t, n_elec);
+    if (t->n_k && !has_bloch_epilogue(kc)) return BLIP_ERR_INVALID_ARG;
+    // the sort clears its histogram itself and overwrites everything else it
+    // reads; no per-electron records (the kernels wrap the positions)
     int *perm = nullptr;
     CK(launch_sort(t->geo, pos, n_elec, scratch, &perm, s));
-    const KernelChoice kc = pick(t, n_elec);
-    EvalParams p{};
-    p.table = t->d_table;
-    p.scales = t->d_scales;
-    p.row_stride = t->row_stride;
-    p.Lreal = t->Lreal;
-    p.nchunk = t->nchunk;
-    const bool grouped = kc.variant == VAR_GROUPED;
-    const bool staged = kc.variant == VAR_STAGED;
-    p.groups = (grouped || staged) ? t->nchunk : (t->nchunk + kc.chunks - 1) / kc.chunks;
-    p.items = (long long)n_elec * p.groups;
-    p.geo = t->geo;
-    p.pos = pos;
-    p.n_elec = n_elec;
+    EvalParams p = make_params(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps, kc);
     p.perm = perm;
-    p.group_major = kc.sort == 2 ? 1 : 0;
-    p.offsets = walker_offsets;
-    p.n_walkers = walker_offsets ? n_walkers : 0;
-    p.values = static_cast<float *>(values);
-    p.grads = static_cast<float *>(grads);
-    p.laps = static_cast<float *>(laps);
-    p.vec_out = (t->Lreal % 4 == 0) && aligned16(values) &&
-                (!grads || (aligned16(grads) && aligned16(laps)));
-    p.status = t->d_status;
-    copy_kpoints(t, p);
-    if (kc.variant == VAR_BULK) {
-        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
-        const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
-        int per_sm = (int)((228 * 1024) / (smem + 1024));
-        per_sm = std::max(1, std::min(per_sm, 4));
-        CK(launch_bulk(p, t->elem, kc.chunks, kc.warps, per_sm, t->sm_count, t->test_stall, s));
-    } else if (grouped) {
-        const int *keys = nullptr, *cell_end = nullptr;
-        sort_views(t->geo, n_elec, scratch, &keys, &cell_end);
-        CK(launch_grouped(p, t->elem, kc.chunks, kc.warps, keys, cell_end, s));
-    } else if (staged) {
-        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
-        const int *keys = nullptr, *cell_end = nullptr;
-        sort_views(t->geo, n_elec, scratch, &keys, &cell_end);
-        const TmaDesc *tm = nullptr;
-        rc = staged_tmap(t, kc.chunks, &tm);
-        if (rc) return rc;
-        CK(launch_staged(p, t->elem, kc.chunks, kc.warps, cell_end, *tm, t->sm_count, t->test_stall,
-                         s));
-    } else if (kc.variant == VAR_SPLIT) {
-        if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
-        CK(launch_split(p, t->elem, s));
-    } else {
-        CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, s));
-    }
-    t->last_stream = s;
-    t->used = true;
-    return BLIP_OK;
+    return launch_choice(t, p, kc, scratch, s);
 }
