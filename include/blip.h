@@ -218,9 +218,10 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort);
 
 /*
  * blip_autotune - time each kernel configuration on this batch shape and keep
- * the fastest for batches of this size class (median of 5 runs, each after a
- * 256 MB scratch write that clears the L2; the scratch is allocated for the
- * call).  Same arguments as blip_eval (the outputs are overwritten).
+ * the fastest for batches of this size class (median of 7 runs, then of 15
+ * more for the configurations within 5 % of the best; each run after a read
+ * sweep of a 256 MB scratch that leaves only its clean lines in L2; the
+ * scratch is allocated for the call).  Same arguments as blip_eval (the outputs are overwritten).
  * Synchronises the stream; must not be called during stream capture.  *chosen receives {variant, chunks, warps, sort}.
  */
 int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker_offsets,

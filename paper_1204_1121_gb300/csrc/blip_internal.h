@@ -178,6 +178,10 @@ cudaError_t launch_split(const EvalParams &p, int elem, cudaStream_t stream);
 cudaError_t launch_sm_update(int n_walkers, int n, float *dinv, const float *rows, const int *cols,
                              float *work, cudaStream_t stream);
 
+// Read bytes of buf through L2 (no writes): afterwards L2 holds clean lines
+// of buf only (the autotuner's cold start).
+cudaError_t launch_l2_sweep(const void *buf, size_t bytes, int sm_count, cudaStream_t stream);
+
 // Table construction kernels (blip_table.cu).
 // Convert rows [row0, row0 + nrows) of a source table [n1*n2*n3][Lreal]
 // (src points at row row0) into the FP32 ghost-plane layout.
