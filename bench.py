@@ -35,16 +35,14 @@ import blip_inputs as bi  # noqa: E402
 # the evaluation kernel on this workload, from ncu, keyed by the SHA-256 of
 # the evaluation-path sources it was measured on (kernel_hash) and by the
 # kernel (variant, chunks); reported as null once those sources change.
-# Filled from the committed summaries under profiles/ (the summaries give
-# the hash of all library sources at capture time, ef85fc96233ef064; the
-# evaluation-path sources are unchanged since).
+# Filled from the committed summaries under profiles/.
 NCU_TRAFFIC = {
     # (kernel source hash, workload, storage, electrons): {(variant, chunks): bytes}
-    ("e4c0ab6b52dbb9b0", "tio2", "f32", 1536): {(9, 1): 275612160 + 12713728,
-                                                (3, 2): 274916864 + 11676928},
+    ("b542d632a27627bf", "tio2", "f32", 1536): {(9, 1): 275618816 + 12643072,
+                                                (3, 2): 274882816 + 11721728},
     # captured with 128 orbitals, scaled x6 to 768 (rows and outputs grow
     # in proportion to the orbital count)
-    ("e4c0ab6b52dbb9b0", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156529408 + 948103936)},
+    ("b542d632a27627bf", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156424960 + 947456768)},
 }
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "c64": 3, "bf16pair": 4}
