@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -33,16 +34,16 @@ import blip_inputs as bi  # noqa: E402
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the evaluation kernel on this workload, from ncu, keyed by the SHA-256 of
-# the evaluation-path sources it was measured on (kernel_hash) and by the
+# the evaluation-path code it was measured on (kernel_hash) and by the
 # kernel (variant, chunks); reported as null once those sources change.
 # Filled from the committed summaries under profiles/.
 NCU_TRAFFIC = {
     # (kernel source hash, workload, storage, electrons): {(variant, chunks): bytes}
-    ("b542d632a27627bf", "tio2", "f32", 1536): {(9, 1): 275618816 + 12643072,
+    ("9adae89b35dae5f9", "tio2", "f32", 1536): {(9, 1): 275618816 + 12643072,
                                                 (3, 2): 274882816 + 11721728},
     # captured with 128 orbitals, scaled x6 to 768 (rows and outputs grow
     # in proportion to the orbital count)
-    ("b542d632a27627bf", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156424960 + 947456768)},
+    ("9adae89b35dae5f9", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156424960 + 947456768)},
 }
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "c64": 3, "bf16pair": 4}
@@ -116,15 +117,24 @@ def touched_sites(grid, lattice, pos):
     return int(mark.sum())
 
 
+def _code_only(text):
+    """Source text without comments and with whitespace runs collapsed, so
+    that comment edits keep the hash."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash():
-    """SHA-256 (16 hex digits) of every CUDA source of the evaluation path
-    (all of the library but the Sherman-Morrison update)."""
+    """SHA-256 (16 hex digits) of the code (comments aside) of every CUDA
+    source of the evaluation path (all of the library but the
+    Sherman-Morrison update)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1204_1121_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh", ".h")) and f != "blip_sm.cu":
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+            with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+                h.update(f.encode() + b"\0" + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

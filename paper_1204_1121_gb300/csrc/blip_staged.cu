@@ -14,7 +14,8 @@
 // orbital components (128 FP32 or 256 16-bit components), laid out
 // [column (5 x 5)][z-row (TZ + 3)][512 bytes].
 //
-// Persistent grid, one CTA per SM: one producer warp and 16 consumer warps.
+// Persistent grid, one CTA per SM: one producer warp and 12 or 16 consumer
+// warps.
 //   * producer: for each tile (static round robin), each part of the tile's
 //     electrons (at most 32, or 24 with TZ = 2, so their weights fit) and
 //     each chunk, waits for a free stage (a ring of 2 stages, or 3 with

@@ -54,10 +54,13 @@ def test_kernel_hash_tracks_the_evaluation_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.kernel_hash() == h0
     f = root / "paper_1204_1121_gb300" / "csrc" / "blip_staged.cu"
-    f.write_text(f.read_text() + "\n")
-    assert bench.kernel_hash() != h0
+    text = f.read_text()
+    f.write_text(text + "\n// a comment and more blank space\n\n")
+    assert bench.kernel_hash() == h0                   # comments do not count
+    f.write_text(text + "\nstatic int unused_probe;\n")
+    assert bench.kernel_hash() != h0                   # code does
+    f.write_text(text)
     # the Sherman-Morrison update is not part of the evaluation path
-    f.write_text(f.read_text()[:-1])
     g = root / "paper_1204_1121_gb300" / "csrc" / "blip_sm.cu"
-    g.write_text(g.read_text() + "\n")
+    g.write_text(g.read_text() + "\nstatic int unused_probe;\n")
     assert bench.kernel_hash() == h0
