@@ -1,6 +1,7 @@
-// Device helpers shared by the evaluation kernels (register gather and bulk
-// copy): the 1-D cubic B-spline factors, the FP64 cell reduction, the 64 x 5
-// combined weights and the unpacking of stored elements.
+// Device helpers shared by the evaluation kernels: the 1-D cubic B-spline
+// factors, the FP64 cell reduction, the 64 x 5 combined weights, the
+// unpacking of stored elements, the packed accumulators and the output
+// stores.
 #pragma once
 
 #include <cuda_bf16.h>

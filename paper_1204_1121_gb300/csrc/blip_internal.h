@@ -105,13 +105,14 @@ struct EvalParams {
 inline int elem_vec(int elem) { return elem == ELEM_F32 ? 4 : 8; }
 inline int elem_bytes(int elem) { return elem == ELEM_F32 ? 4 : 2; }
 
-// Launch the register-gather kernel (variant VAR_REGISTER, or
-// VAR_REGISTER_PIPE for the software-pipelined loop).  chunks in {1, 2, 3}
-// (1 for 16-bit elements); warps in [1, 16].
+// Launch a register-gather kernel: variants VAR_REGISTER, _PIPE, _ROLLED,
+// _L1, _LOCKSTEP and _PIPE3.  chunks in {1, 2, 3} (1 for 16-bit elements,
+// and for _PIPE3); warps in [1, 16].
 cudaError_t launch_eval(const EvalParams &p, int elem, int variant, int chunks, int warps,
                         cudaStream_t stream);
 
-// Register-gather instantiations (blip_reg_*.cu): pipe 0..3 as the variants.
+// Register-gather instantiations (blip_reg_*.cu); pipe 0-5: batch, pipelined,
+// rolled, L1-shared, lockstep, two batches in flight.
 cudaError_t launch_register_f32_c1(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
 cudaError_t launch_register_f32_c2(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
 cudaError_t launch_register_f32_c3(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
