@@ -198,17 +198,22 @@ int blip_info(blip_table t, long long out[8]);
  *                 per (electron, chunk), one a_1 slab of 16 sites each, all
  *                 16 rows loaded at once, the partial sums added in a fixed
  *                 order (agrees with the other variants to rounding, not
- *                 bitwise); not with k-points
+ *                 bitwise); not with k-points;
+ *             11: as 9 with a grid of resident warps that walk the (electron,
+ *                 chunk) items; each warp prefetches the next electron's
+ *                 position (cp.async) and runs its FP64 wrap while the
+ *                 current rows are in flight (FP32 tables, one chunk per
+ *                 warp; not with k-points)
  *   chunks     variants 1, 3, 4, 6, 7: orbital chunks (32 lanes x 16 bytes) per
- *              warp, 1..3 (1 for 16-bit storage); variant 9: 1; variant 2: consumer warps
+ *              warp, 1..3 (1 for 16-bit storage); variants 9, 11: 1; variant 2: consumer warps
  *              per CTA, 1..8; variant 5: electrons per group, 2 or 4;
  *              variant 8: tile cells along a_3, 2 or 4; variant 10: 1
- *   warps      variants 1, 3, 4, 6, 7, 9: warps per block, 1..16; variant 2:
+ *   warps      variants 1, 3, 4, 6, 7, 9, 11: warps per block, 1..16; variant 2:
  *              shared-memory pipeline stages, 2..32; variant 5: warps per
  *              block, 1..8; variant 8: consumer warps per CTA, 12 or 16;
  *              variant 10: 4
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2
- *              reuse for large batches); 2 (variants 1, 3, 4, 9): sorted, and
+ *              reuse for large batches); 2 (variants 1, 3, 4, 9, 11): sorted, and
  *              the warps' work ordered by orbital chunk group first, so the
  *              warps in flight cover more electrons with a smaller slice of
  *              each row
@@ -245,8 +250,8 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
  *            koffs[n_k] = n_orb
  * The phase uses the unwrapped fractional coordinates, reduced mod 1 in
  * FP64.  Errors: INVALID_ARG, UNSUPPORTED_DTYPE (real tables).  The bulk-copy,
- * staged-tile and split-stencil kernels (variants 2, 8 and 10) have no
- * Bloch epilogue and are not used while k-points are set.
+ * staged-tile, split-stencil and persistent kernels (variants 2, 8, 10 and
+ * 11) have no Bloch epilogue and are not used while k-points are set.
  */
 int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koffs);
 

@@ -224,7 +224,8 @@ int staged_tmap(blip_table_s *t, int tz, const TmaDesc **out)
 // The bulk-copy, staged-tile and split-stencil kernels have no Bloch epilogue.
 bool has_bloch_epilogue(const KernelChoice &kc)
 {
-    return kc.variant != VAR_BULK && kc.variant != VAR_STAGED && kc.variant != VAR_SPLIT;
+    return kc.variant != VAR_BULK && kc.variant != VAR_STAGED && kc.variant != VAR_SPLIT &&
+           kc.variant != VAR_REGISTER_PERSIST;
 }
 
 // Launch parameters of an evaluation with kernel choice kc; the evaluation
@@ -286,6 +287,9 @@ int launch_choice(blip_table_s *t, const EvalParams &p, const KernelChoice &kc, 
                          stream));
     } else if (kc.variant == VAR_SPLIT) {
         CK(launch_split(p, t->elem, stream));
+    } else if (kc.variant == VAR_REGISTER_PERSIST) {
+        if (t->elem != ELEM_F32) return BLIP_ERR_INVALID_ARG;
+        CK(launch_persist(p, kc.warps, t->sm_count, stream));
     } else {
         CK(launch_eval(p, t->elem, kc.variant, kc.chunks, kc.warps, stream));
     }
@@ -614,6 +618,10 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         // two batches in flight: FP32 tables, one chunk per warp
         if (t->elem != ELEM_F32 || chunks != 1) return BLIP_ERR_INVALID_ARG;
         if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
+    } else if (variant == VAR_REGISTER_PERSIST) {
+        // as 9, resident warps; no Bloch epilogue
+        if (t->elem != ELEM_F32 || chunks != 1 || t->n_k) return BLIP_ERR_INVALID_ARG;
+        if (warps < 1 || warps > 16) return BLIP_ERR_INVALID_ARG;
     } else if (variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE || variant == VAR_REGISTER_ROLLED ||
         variant == VAR_REGISTER_L1 || variant == VAR_REGISTER_LOCKSTEP) {
         const int max_chunks = t->elem == ELEM_F32 ? 3 : 1;
@@ -639,7 +647,8 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
     // sort 2: sorted, and the register kernels' items ordered chunk group
     // slowest
     const bool order_ok = variant == VAR_REGISTER || variant == VAR_REGISTER_PIPE ||
-                          variant == VAR_REGISTER_ROLLED || variant == VAR_REGISTER_PIPE3;
+                          variant == VAR_REGISTER_ROLLED || variant == VAR_REGISTER_PIPE3 ||
+                          variant == VAR_REGISTER_PERSIST;
     if (sort != 0 && sort != 1 && !(sort == 2 && order_ok)) return BLIP_ERR_INVALID_ARG;
     t->auto_mode = false;
     t->choice = KernelChoice{variant, chunks, warps, sort};
@@ -670,6 +679,11 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
                 if (c == 1 && t->elem == ELEM_F32) {
                     cands.push_back(KernelChoice{VAR_REGISTER_PIPE3, c, w, srt});
                     if (srt && t->nchunk > c) cands.push_back(KernelChoice{VAR_REGISTER_PIPE3, c, w, 2});
+                    if (!t->n_k) {
+                        cands.push_back(KernelChoice{VAR_REGISTER_PERSIST, c, w, srt});
+                        if (srt && t->nchunk > c)
+                            cands.push_back(KernelChoice{VAR_REGISTER_PERSIST, c, w, 2});
+                    }
                 }
                 if (srt && t->nchunk > c) {       // several chunk groups: try their order too
                     cands.push_back(KernelChoice{VAR_REGISTER, c, w, 2});

@@ -237,16 +237,21 @@ __device__ __forceinline__ int column_row(const Geometry &geo, int i0, int i1, i
 // FP32 offsets for stencil_weights_warp.
 // GEO: 0 = FP64 wrap here, 1 = FP64 wrap + Bloch phases, 2 = read the
 // per-slot record the sort pre-pass made (its FP64 wrap already done).
+// src, if given, replaces the global source: electron e's 3 coordinates
+// (GEO 0, 1) or slot's record (GEO 2), e.g. a copy prefetched into shared
+// memory.
 template <int GEO = 0>
 __device__ __forceinline__ int stencil_geometry_warp(const EvalParams &p, int e, int lane,
                                                      WarpSlice &ws, float &t0, float &t1,
-                                                     float &t2, int slot = -1)
+                                                     float &t2, int slot = -1,
+                                                     const void *src = nullptr)
 {
     constexpr bool BLOCH = GEO == 1;
     if constexpr (GEO == 2) {
         // geometry already reduced in FP64 by the sort pre-pass
-        const int4 gi = *reinterpret_cast<const int4 *>(p.georec + slot);
-        const float4 gt = *reinterpret_cast<const float4 *>(&p.georec[slot].t[0]);
+        const ElecGeo *rec = src ? static_cast<const ElecGeo *>(src) : p.georec + slot;
+        const int4 gi = *reinterpret_cast<const int4 *>(rec);
+        const float4 gt = *reinterpret_cast<const float4 *>(&rec->t[0]);
         t0 = gt.x;
         t1 = gt.y;
         t2 = gt.z;
@@ -259,7 +264,7 @@ __device__ __forceinline__ int stencil_geometry_warp(const EvalParams &p, int e,
     float ta = 0.0f;
     double ua = 0.0;
     if (lane < 3) {
-        const double *r = p.pos + 3 * (size_t)e;
+        const double *r = src ? static_cast<const double *>(src) : p.pos + 3 * (size_t)e;
         bad = wrap_axis(p.geo, lane, r[0], r[1], r[2], ia, ta, &ua);
     }
     bad = __reduce_or_sync(FULL, bad);

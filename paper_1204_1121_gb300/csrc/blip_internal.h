@@ -24,8 +24,10 @@ enum Variant {
     VAR_STAGED = 8,           // 2 x 2 x TZ cell tiles: union rows staged in shared
                               // memory, every electron of the tile contracted there
     VAR_REGISTER_PIPE3 = 9,   // as 3 with two batches in flight (FP32, 1 chunk per warp)
-    VAR_SPLIT = 10            // 4 warps per (electron, chunk), one a_1 slab of the
+    VAR_SPLIT = 10,           // 4 warps per (electron, chunk), one a_1 slab of the
                               // stencil each: one round of latency (small launches)
+    VAR_REGISTER_PERSIST = 11 // as 9 with resident warps that walk the items and
+                              // prefetch the next electron's geometry (no k-points)
 };
 
 constexpr int kMaxKpoints = 16;
@@ -118,6 +120,10 @@ cudaError_t launch_register_f32_c2(const EvalParams &p, int warps, int pipe, cud
 cudaError_t launch_register_f32_c3(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
 cudaError_t launch_register_bf16(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
 cudaError_t launch_register_f16(const EvalParams &p, int warps, int pipe, cudaStream_t stream);
+
+// Persistent two-batch register kernel (blip_persist.cu): FP32 tables, one
+// chunk per warp, no Bloch epilogue; at most as many blocks as fit at once.
+cudaError_t launch_persist(const EvalParams &p, int warps, int sm_count, cudaStream_t stream);
 
 // Launch the bulk-copy kernel: tw chunks per tile (consumer warps, 1..8),
 // `stages` shared-memory stages, ctas_per_sm persistent CTAs per SM.

@@ -101,6 +101,7 @@ def test_kernel_configs_bitwise_identical(pb):
     cfgs += [(8, tz, cw, 1) for tz in (2, 4) for cw in (12, 16)]
     cfgs += [(v, c, w, 2) for v in (1, 3, 4) for c in (1, 2, 3) for w in (1, 8)]
     cfgs += [(9, 1, w, s) for w in (1, 4, 16) for s in (0, 1, 2)]
+    cfgs += [(11, 1, w, s) for w in (1, 4, 16) for s in (0, 1, 2)]
     for cfg in cfgs:
         t.set_kernel(*cfg)
         out = gpu_eval(t, pos)
