@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the access-pattern probe")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -443,6 +444,31 @@ def main():
             "gpu_launches": K * (6 if chosen[3] else 1), "kernel_choice": list(chosen),
             "status": st,
             "wall_s_timed_region": wall}
+
+    if not args.no_probe and args.storage in ("f32", "c64"):
+        # the access pattern's own time (blip_probe_gather): the evaluation's
+        # item walk, FP64 geometry, row loads and output stores without the
+        # weights and FMAs, timed like the steps above
+        def probe_ms(store):
+            for k in range(3):
+                flush_l2(k)
+                t.probe_gather(dpos, out=out, store=store)
+            pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(K)]
+            for k in range(K):
+                flush_l2(k)
+                pe[k][0].record(stream)
+                t.probe_gather(dpos, out=out, store=store)
+                pe[k][1].record(stream)
+            torch.cuda.synchronize()
+            return statistics.mean(a.elapsed_time(b) for a, b in pe)
+        g_ms, gs_ms = probe_ms(False), probe_ms(True)
+        line["pattern_ceiling"] = {
+            "gather_us": 1e3 * g_ms, "gather_store_us": 1e3 * gs_ms, "kernel_us": 1e3 * ms,
+            "kernel_frac_of_ceiling": gs_ms / ms,
+            "ceiling_frac_of_copy": bytes_alg / (gs_ms / 1e3) / 1e9 / peak,
+            "what": "blip_probe_gather on the same positions (input order): geometry, the 64 row "
+                    "loads per item and (gather_store) the output stores, without the arithmetic"}
 
     if not args.no_e2e:
         # end to end through the host-buffer entry point: H2D positions,

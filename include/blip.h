@@ -150,6 +150,29 @@ int blip_eval_host(blip_table t, const double *pos, int n_elec, const int *walke
  */
 int blip_status(blip_table t, int *device_status);
 
+/*
+ * blip_probe_gather - a measurement aid, not an evaluation: the memory
+ * traffic of one evaluation launch without its arithmetic.  For every
+ * (electron, 512-byte chunk of components) item it runs the item walk, the
+ * FP64 position wrap and the 64 stencil-row loads of the persistent
+ * register kernel (variant 11, 8 warps per block, input order), leaves out
+ * the weights and the contraction (Eq. 11.12.24.1), folds the loaded words
+ * into one word per lane, and, if store_outputs != 0, writes that word to
+ * the item's five output slices with the same streaming stores.  Timed next
+ * to blip_eval on the same positions it gives the time the access pattern
+ * itself takes (scattered 4-row columns in HBM, L2 reuse, output stores):
+ * the ceiling for any kernel that reads the table in this order.  The
+ * compiler is free to give the probe fewer registers (and so more resident
+ * warps) than the kernel it mirrors.
+ *   pos      device [n_elec][3] FP64
+ *   values, grads, laps  device, laid out as for blip_eval; written only
+ *            when store_outputs != 0, with meaningless contents
+ * FP32 tables only; k-points are ignored.  Errors: INVALID_ARG,
+ * UNSUPPORTED_DTYPE (16-bit storage), CUDA.
+ */
+int blip_probe_gather(blip_table t, const double *pos, int n_elec, void *values, void *grads,
+                      void *laps, int store_outputs, void *stream);
+
 /* blip_destroy - free the table and everything it owns (NULL is accepted). */
 int blip_destroy(blip_table t);
 

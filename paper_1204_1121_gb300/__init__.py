@@ -48,6 +48,7 @@ EXPORTED = {
     "blip_set_kpoints": (I, [P, I, P, P]),
     "blip_sm_update": (I, [I, I, P, P, P, P, P]),
     "blip_test_stall_pipeline": (I, [P, I]),
+    "blip_probe_gather": (I, [P, P, I, P, P, P, I, P]),
 }
 
 _lock = threading.Lock()
@@ -244,6 +245,25 @@ class BlipTable:
                                          P(vals.data_ptr()) if vals is not None else None,
                                          int(sort), _stream_ptr(stream)), "blip_eval_ratio")
         return ratio, vals
+
+    def probe_gather(self, pos, out=None, store=True, stream=None):
+        """Measurement probe (``blip_probe_gather``): the row loads (and, if
+        ``store``, the output stores) of an evaluation of ``pos`` without its
+        arithmetic.  ``out``: outputs from ``alloc_outputs`` (written with
+        meaningless contents)."""
+        import torch
+        if not (pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous()):
+            raise TypeError("pos must be a contiguous CUDA float64 tensor")
+        n = pos.shape[0]
+        v = g = lp = None
+        if store:
+            v, g, lp = out if out is not None else self.alloc_outputs(n, False, pos.device)
+        _check(self._lib.blip_probe_gather(self._h, P(pos.data_ptr()), n,
+                                           P(v.data_ptr()) if v is not None else None,
+                                           P(g.data_ptr()) if g is not None else None,
+                                           P(lp.data_ptr()) if lp is not None else None,
+                                           1 if store else 0, _stream_ptr(stream)),
+               "blip_probe_gather")
 
     def status(self):
         s = ctypes.c_int(0)

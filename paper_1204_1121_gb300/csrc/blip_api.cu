@@ -515,6 +515,23 @@ int blip_eval(blip_table t, const double *pos, int n_elec, const int *walker_off
                        static_cast<cudaStream_t>(stream), pick(t, n_elec));
 }
 
+int blip_probe_gather(blip_table t, const double *pos, int n_elec, void *values, void *grads,
+                      void *laps, int store_outputs, void *stream)
+{
+    if (!t || n_elec < 0 || (n_elec > 0 && !pos)) return BLIP_ERR_INVALID_ARG;
+    if (store_outputs && n_elec > 0 && (!values || !grads || !laps)) return BLIP_ERR_INVALID_ARG;
+    if (t->elem != ELEM_F32) return BLIP_ERR_UNSUPPORTED_DTYPE;
+    if (n_elec == 0) return BLIP_OK;
+    const KernelChoice kc{VAR_REGISTER_PERSIST, 1, 8, 0};
+    EvalParams p = make_params(t, pos, n_elec, nullptr, 0, store_outputs ? values : nullptr,
+                               store_outputs ? grads : nullptr, store_outputs ? laps : nullptr, kc);
+    p.n_k = 0;                       // the phases are arithmetic the probe leaves out
+    CK(launch_probe(p, kc.warps, t->sm_count, store_outputs != 0, static_cast<cudaStream_t>(stream)));
+    t->last_stream = static_cast<cudaStream_t>(stream);
+    t->used = true;
+    return BLIP_OK;
+}
+
 // Device address of a pinned (page-locked) host buffer, or nullptr if p is
 // ordinary pageable memory.
 void *mapped_device_ptr(const void *p)

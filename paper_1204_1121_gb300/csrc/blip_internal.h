@@ -124,6 +124,9 @@ cudaError_t launch_register_f16(const EvalParams &p, int warps, int pipe, cudaSt
 // Persistent two-batch register kernel (blip_persist.cu): FP32 tables, one
 // chunk per warp, no Bloch epilogue; at most as many blocks as fit at once.
 cudaError_t launch_persist(const EvalParams &p, int warps, int sm_count, cudaStream_t stream);
+// The measurement probe of the same kernel (input order, FP32): geometry and
+// row loads without the arithmetic; store = also write the five outputs.
+cudaError_t launch_probe(const EvalParams &p, int warps, int sm_count, bool store, cudaStream_t stream);
 
 // Launch the bulk-copy kernel: tw chunks per tile (consumer warps, 1..8),
 // `stages` shared-memory stages, ctas_per_sm persistent CTAs per SM.

@@ -109,7 +109,11 @@ __device__ __forceinline__ void next_geometry(const EvalParams &p, PersistSlice 
     }
 }
 
-template <bool VONLY, int GEO>
+// PROBE: 0 evaluates; 1 and 2 are the measurement probe behind
+// blip_probe_gather: the same geometry, row loads and item walk with the
+// weights and the contraction left out (the loaded words are folded into one
+// word per lane), and for 2 the five output slices stored as usual.
+template <bool VONLY, int GEO, int PROBE = 0>
 __global__ void __launch_bounds__(512) blip_eval_persist(EvalParams p)
 {
     constexpr int VEC = 4;
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(512) blip_eval_persist(EvalParams p)
             for (int v = 0; v < VEC; ++v) acc[k][v] = 0.0f;
         AccPairs<VEC> a5;
         pairs_zero(a5);
+        unsigned fold = 0;                        // PROBE: the loaded words, folded
         {
             // the next item's source, into the slice while this item's rows fly
             const ItemPos nx = step_item(p, it, ps.dq, ps.dr);
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(512) blip_eval_persist(EvalParams p)
                 const int pt = q * RB + r;
                 buf[q][r] = ldg_stream(tbase + (size_t)(ws.colrow[pt >> 2] + (pt & 3)) * rowb + coff);
             }
-        stencil_weights_warp(p, t0, t1, t2, lane, ws);   // overlaps the first loads
+        if constexpr (!PROBE) stencil_weights_warp(p, t0, t1, t2, lane, ws);   // overlaps the first loads
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             if (b + NBUF - 1 < NB) {
@@ -208,6 +213,11 @@ __global__ void __launch_bounds__(512) blip_eval_persist(EvalParams p)
             }
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
+                if constexpr (PROBE) {
+                    const uint4 u = buf[b % NBUF][r];
+                    fold ^= u.x ^ u.y ^ u.z ^ u.w;
+                    continue;
+                }
                 const int pt = b * RB + r;
                 const float4 w = ws.w4[pt];
                 const float wl = VONLY ? 0.0f : ws.wl[pt];
@@ -234,15 +244,28 @@ __global__ void __launch_bounds__(512) blip_eval_persist(EvalParams p)
                 }
             }
         }
-        if constexpr (!VONLY) pairs_out(a5, acc);
-        store_chunk<VEC, VONLY>(p, e, grp, lane, acc);
+        if constexpr (PROBE == 1) {
+            // no stores: the fold is written only under a condition the
+            // compiler cannot decide (never true here: the probe passes no
+            // outputs), so every load stays
+            if (p.values && fold == 0x9e3779b9u) p.values[lane] = __uint_as_float(fold);
+        } else if constexpr (PROBE == 2) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[k][v] = __uint_as_float(fold);
+            store_chunk<VEC, VONLY>(p, e, grp, lane, acc);
+        } else {
+            if constexpr (!VONLY) pairs_out(a5, acc);
+            store_chunk<VEC, VONLY>(p, e, grp, lane, acc);
+        }
         it = step_item(p, it, ps.dq, ps.dr);
         if (it.maj >= major_count(p)) break;
         __syncwarp();                             // the weights are read by every lane
     }
 }
 
-template <bool VONLY, int GEO>
+template <bool VONLY, int GEO, int PROBE = 0>
 cudaError_t launch_persist_t(const EvalParams &p, int warps, int sm_count, cudaStream_t stream)
 {
     const size_t smem = sizeof(PersistSlice) * (size_t)warps;
@@ -251,7 +274,7 @@ cudaError_t launch_persist_t(const EvalParams &p, int warps, int sm_count, cudaS
     static int occ[17] = {0};
     if (occ[warps] == 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blip_eval_persist<VONLY, GEO>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blip_eval_persist<VONLY, GEO, PROBE>,
                                                           32 * warps, smem) != cudaSuccess ||
             nb < 1)
             nb = 1;
@@ -260,7 +283,7 @@ cudaError_t launch_persist_t(const EvalParams &p, int warps, int sm_count, cudaS
     const long long resident = (long long)occ[warps] * (sm_count > 0 ? sm_count : 1);
     if (blocks > resident) blocks = resident;
     if (blocks < 1) blocks = 1;
-    blip_eval_persist<VONLY, GEO><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
+    blip_eval_persist<VONLY, GEO, PROBE><<<(unsigned)blocks, 32 * warps, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -275,6 +298,17 @@ cudaError_t launch_persist(const EvalParams &p, int warps, int sm_count, cudaStr
     }
     if (p.grads) return launch_persist_t<false, 0>(p, warps, sm_count, stream);
     return launch_persist_t<true, 0>(p, warps, sm_count, stream);
+}
+
+cudaError_t launch_probe(const EvalParams &p, int warps, int sm_count, bool store, cudaStream_t stream)
+{
+    if (p.n_k || p.georec || p.perm || p.groups != p.nchunk || warps < 1 || warps > 16)
+        return cudaErrorInvalidValue;
+    if (store) {
+        if (!p.values || !p.grads || !p.laps) return cudaErrorInvalidValue;
+        return launch_persist_t<false, 0, 2>(p, warps, sm_count, stream);
+    }
+    return launch_persist_t<false, 0, 1>(p, warps, sm_count, stream);
 }
 
 }  // namespace blip

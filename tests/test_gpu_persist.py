@@ -10,6 +10,8 @@ input order and both sorted orders), non-finite and far positions between
 ordinary ones (the path that skips the rows and takes the next geometry
 synchronously), ragged walker batches, values only, a CUDA graph, the
 full-size TiO2-shaped headline batch, and the configurations it refuses.
+The measurement probe built from the same kernel (blip_probe_gather) is
+checked to load exactly the rows an evaluation loads.
 """
 import numpy as np
 import pytest
@@ -175,3 +177,48 @@ def test_persist_rejections(pb):
     tc.set_kpoints(np.zeros((1, 3)), [0, 8])           # no Bloch epilogue: choice reset
     with pytest.raises(Exception):
         tc.set_kernel(11, 1, 4, 0)
+
+
+def test_probe_gather_reads_the_evaluation_rows(pb):
+    """blip_probe_gather folds (XOR) the 16 bytes each lane loads from the 64
+    stencil rows of its (electron, chunk) item.  With output stores on, the
+    folded word lands in the item's value slice, so it can be checked exactly
+    against the same fold over the FP32-rounded coefficients of the 64 sites
+    around each position: the probe reads the rows an evaluation reads.
+    Without stores the outputs are left untouched."""
+    grid = (9, 8, 10)
+    lat = pins.triclinic_lattice()
+    L = 700
+    tab = bi.smooth_random_table(grid, L, seed=69)
+    pos = bi.uniform_positions(lat, 3000, seed=69)
+    t = pb.BlipTable(grid, lat, tab)
+    dpos = torch.from_numpy(pos).cuda()
+    sentinel = 0x7F7F7F7F
+    out = t.alloc_outputs(len(pos))
+    for o in out:
+        o.view(torch.int32).fill_(sentinel)
+    t.probe_gather(dpos, out=out, store=False)
+    torch.cuda.synchronize()
+    assert all(bool((o.view(torch.int32) == sentinel).all()) for o in out)
+    t.probe_gather(dpos, out=out, store=True)
+    torch.cuda.synchronize()
+    got = out[0].view(torch.int32).cpu().numpy().view(np.uint32)
+
+    n = np.array(grid)
+    u = np.linalg.solve(lat.T, pos.T).T               # r = u @ lat
+    g = (u - np.floor(u)) * n
+    base = np.floor(g).astype(np.int64) % n
+    words = tab.astype(np.float32).view(np.uint32)   # [n1][n2][n3][L]
+    ref = np.zeros((len(pos), L), dtype=np.uint32)
+    for kx in range(4):
+        for ky in range(4):
+            for kz in range(4):
+                m = (base + np.array([kx, ky, kz]) - 1) % n
+                ref ^= words[m[:, 0], m[:, 1], m[:, 2]]
+    lanes = ref.reshape(len(pos), -1, 4)             # 4 components per lane
+    fold = np.bitwise_xor.reduce(lanes, axis=2)
+    assert np.array_equal(got.reshape(len(pos), -1, 4), np.repeat(fold[:, :, None], 4, axis=2))
+    assert t.status() == 0
+    t16 = pb.BlipTable(grid, lat, tab, storage=pb.BF16)
+    with pytest.raises(Exception):
+        t16.probe_gather(dpos, out=t16.alloc_outputs(len(pos)))
