@@ -374,6 +374,14 @@ def main():
     def step():
         t.eval(dpos, doffs, out=out)
 
+    def hold_queue(steps):
+        # a device-side wait ahead of timed launches: the host enqueues them
+        # all while it runs, so a host stall cannot leave the GPU idle inside
+        # a step's CUDA-event window
+        sleep = getattr(torch.cuda, "_sleep", None)
+        if sleep is not None:
+            sleep(int(2.0e9 * (0.005 + 0.001 * steps)))
+
     for k in range(max(3, args.warmup)):
         flush_l2(k)
         step()
@@ -390,6 +398,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
+    hold_queue(K)
     for k in range(K):
         flush_l2(k)
         evs[k][0].record(stream)
@@ -455,6 +464,7 @@ def main():
                 t.probe_gather(dpos, out=out, store=store)
             pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(K)]
+            hold_queue(K)
             for k in range(K):
                 flush_l2(k)
                 pe[k][0].record(stream)
@@ -506,6 +516,7 @@ def main():
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 5
+        hold_queue(reps)
         a.record(stream)
         for _ in range(reps):
             g.launch()
