@@ -456,10 +456,11 @@ def main():
             "status": st,
             "wall_s_timed_region": wall}
 
-    if not args.no_probe and args.storage in ("f32", "c64"):
+    if not args.no_probe and args.storage in ("f32", "c64") and chosen[3] == 0:
         # the access pattern's own time (blip_probe_gather): the evaluation's
         # item walk, FP64 geometry, row loads and output stores without the
-        # weights and FMAs, timed like the steps above
+        # weights and FMAs, timed like the steps above (the probe walks the
+        # batch in input order, so it is the ceiling of unsorted launches)
         def probe_ms(store):
             for k in range(3):
                 flush_l2(k)
