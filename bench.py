@@ -69,7 +69,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
-    ap.add_argument("--no-probe", action="store_true", help="skip the access-pattern probe")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="skip the access-pattern probe and the SGEMM peak")
+    ap.add_argument("--warm", action="store_true",
+                    help="no L2 flush between steps (tables that fit in L2)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -94,7 +97,8 @@ def describe(w, args, E):
                      f"{'complex' if w.is_complex else 'real'} orbitals, {E} positions per step"
                      + (f" ({w.n_walkers} walkers)" if w.n_walkers > 1 else " (all at once)"),
          "electrons": E, "orbitals": w.n_orb, "storage": args.storage,
-         "l2": "flushed between steps (512 MB write + 512 MB read, outside the event window)",
+         "l2": "warm (no flush between steps)" if args.warm else
+               "flushed between steps (512 MB write + 512 MB read, outside the event window)",
          "positions": "uniform in cell" if w.uniform_n else "walker configs + N(0,0.3^2) moves"}
     return d
 
@@ -138,6 +142,33 @@ def kernel_hash():
             with open(os.path.join(csrc, f), encoding="utf-8") as fh:
                 h.update(f.encode() + b"\0" + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
+
+
+def sgemm_tflops(n=8192, reps=5):
+    """Measured FP32 (CUDA-core) throughput of this GPU: cuBLAS SGEMM n^3 with
+    TF32 off, best of `reps` CUDA-event timings.  Reported beside the FP32
+    peak derived from unit counts and the clock."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        g = torch.Generator(device="cuda").manual_seed(0)
+        a = torch.randn((n, n), generator=g, device="cuda")
+        b = torch.randn((n, n), generator=g, device="cuda")
+        c = torch.empty((n, n), device="cuda")
+        for _ in range(2):
+            torch.matmul(a, b, out=c)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def measured_peaks():
@@ -376,6 +407,8 @@ def main():
     flush_rd = torch.ones(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def flush_l2(k):
+        if args.warm:                  # warm L2: the table stays cached between steps
+            return None
         flush.fill_(float(k))
         return flush_rd.sum()
 
@@ -420,6 +453,7 @@ def main():
     clocks = sampler.stop()
     per = [a.elapsed_time(b) for a, b in evs]
     ms = replicas.max_over_ranks(statistics.mean(per))
+    ms_median = replicas.max_over_ranks(statistics.median(per))
     evals = E * w.n_orb
     value = world * evals / (ms / 1e3)
 
@@ -447,6 +481,10 @@ def main():
         roof = {"bound": "alu", "achieved": alu_ach, "peak": f32_peak, "unit": "TFLOP/s",
                 "frac": alu_ach / f32_peak, "traffic": rec,
                 "peak_kind": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x 2.07 GHz"}
+        if not args.no_probe:
+            sg = sgemm_tflops()
+            roof["fp32_sgemm_tflops"] = sg
+            roof["frac_of_sgemm"] = alu_ach / sg
     roof.update({"algorithmic_bytes_per_launch": bytes_alg, "touched_sites": U,
                  "fp32_flop_per_launch": flops, "kernel_source_hash": kh,
                  "hbm_frac": hbm_ach / peak, "alu_frac": alu_ach / f32_peak,
@@ -456,7 +494,8 @@ def main():
 
     line = {"metric": "orbital*electron evals/s (val+grad+lap)", "value": value,
             "unit": "orbital*electron evals/s", "n_gpus": world, "steps": K,
-            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "ms_median": ms_median,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": describe(w, args, E), "roofline": roof, "clocks": clocks,
             "gpu_launches": K * (6 if chosen[3] else 1), "kernel_choice": list(chosen),
