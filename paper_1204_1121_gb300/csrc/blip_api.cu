@@ -747,7 +747,7 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
         cudaEventElapsedTime(&ms, e0, e1);
         return r;
     };
-    // round 1: every candidate, median of 7 runs
+    // first pass: every candidate, median of 7 runs
     std::vector<std::pair<float, KernelChoice>> med;
     for (const KernelChoice &kc : cands) {
         rc = eval_device(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps, s, kc);
@@ -760,7 +760,7 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     }
     KernelChoice bestc = cands[0];
     if (rc == 0) {
-        // round 2: the candidates within 5 % of the best, 15 more runs each,
+        // second pass: the candidates within 5 % of the best, 15 more runs each,
         // interleaved so that slow drifts of the clock hit all of them alike
         std::sort(med.begin(), med.end(),
                   [](const std::pair<float, KernelChoice> &a, const std::pair<float, KernelChoice> &b) {
