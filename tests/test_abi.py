@@ -5,7 +5,6 @@ import os
 import re
 
 import numpy as np
-import pytest
 
 import paper_1204_1121_gb300 as pb
 

@@ -263,7 +263,6 @@ def test_empty_batch_and_bad_arguments(pb):
     v, g, lp = t.eval(e)
     assert v.shape == (0, 3)
     L = pb.lib()
-    import ctypes
     assert L.blip_eval(t.handle, None, 5, None, 0, None, None, None, None) == -1
     assert L.blip_set_kernel(t.handle, 1, 4, 8, 0) == -1
     assert L.blip_set_kernel(t.handle, 1, 1, 0, 0) == -1

@@ -10,7 +10,6 @@ import functools
 import os
 import subprocess
 
-import numpy as np
 import pytest
 
 import oracle

@@ -4,7 +4,6 @@ collective on the data path)."""
 import os
 import socket
 
-import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -20,7 +19,6 @@ def _free_port():
 
 
 def _worker(rank, world, port, out):
-    import torch
     import torch.distributed as dist
 
     import blip_inputs as bi
