@@ -7,17 +7,20 @@
 // In the one-electron-per-warp kernels every warp begins with a serial chain
 // that keeps none of its rows in flight: the position load, the FP64 wrap
 // (a slow pipe on this part) and only then the first row loads.  Here a grid
-// of resident warps walks the (electron, chunk) items with a stride; while
-// the rows of the current item are in flight a warp
-//   * copies the next item's position (or its sort record, and its output
-//     index) into its shared slice with cp.async, right after issuing its
-//     third row batch, and
-//   * once the last row batch of the current item is issued (the slice's
-//     column rows are then free), runs the next item's FP64 wrap and writes
-//     its column rows, offsets and status into the slice,
+// of resident warps walks the (electron, chunk) items with a stride; for
+// each item a warp
+//   * first starts a cp.async copy of the next item's position (or its sort
+//     record, and its output index) into its shared slice, so the copy
+//     flies with the item's row loads (issued from within the row loop it
+//     made the compiler spill registers), and
+//   * once the last row batch of the current item is issued and a batch
+//     contracted (the slice's column rows are then free), runs the next
+//     item's FP64 wrap and writes its column rows, offsets and status into
+//     the slice,
 // so the next item's first two batches go out as soon as the current item
-// is stored.  Not for Bloch tables: the phases of the next electron would
-// overwrite the current one's before its store.
+// is stored.  Items are walked in 32-bit (major, minor) steps.  Not for
+// Bloch tables: the phases of the next electron would overwrite the current
+// one's before its store.
 #include "blip_device.cuh"
 
 namespace blip {
