@@ -282,3 +282,80 @@ def check_translation(ev=oracle.eval_stencil):
         for x, y in zip(base, shifted):
             err = max(err, np.abs(x - y).max() / (1 + np.abs(x).max()))
     return err
+
+
+# ---------------------------------------------------------------------------
+# 8. the rounding scale C_o = sum_s |W_o(s)| |a_ls| that the oracle returns
+#    beside every output (the GPU parity bounds are multiples of it)
+# ---------------------------------------------------------------------------
+
+def check_absmag_vs_bruteforce(ev=oracle.eval_stencil):
+    """C_o of the stencil oracle against Oracle B's independent sum over
+    every (site, image) pair of |W_k| |a_ls| (Eqs. 11.12.24.1, 11.12.24.2:
+    each pair is one term, its weight taken after the Jacobian contraction),
+    on triclinic tiny grids with coefficients of both signs, for all five
+    output kinds and both normalisations."""
+    lat = triclinic_lattice()
+    err = 0.0
+    for grid, norm in (((4, 4, 4), 0), ((5, 4, 7), 1), ((7, 6, 5), 0)):
+        n = np.array(grid, dtype=np.float64)
+        tab = RNG.normal(size=grid + (3,))
+        u = np.concatenate([RNG.uniform(-2.0, 3.0, size=(8, 3)),
+                            (RNG.integers(0, 8, size=(2, 3)) % n) / n])
+        pos = frac_to_cart(lat, u)
+        _, _, _, mag = ev(grid, lat, tab, pos, norm=norm, absmag=True)
+        ref = brute.absmag_brute(grid, lat, tab, pos, norm=norm)
+        err = max(err, float(np.max(np.abs(mag - ref) / (np.abs(ref) + 1e-300))))
+    return err
+
+
+def _exact_1d(t):
+    """Exact (b, b', b'') of the 4 stencil sites at offset t in {0, 1/2}:
+    site k sits at grid distance t + 1 - k, and B, B', B'' at the distances
+    1, 0, -1, -2 and 3/2, 1/2, -1/2, -3/2 are the rationals of the golden
+    B-spline table."""
+    from fractions import Fraction as F
+    if t == 0:
+        return ([F(1, 6), F(2, 3), F(1, 6), F(0)], [F(-1, 2), F(0), F(1, 2), F(0)],
+                [F(1), F(-2), F(1), F(0)])
+    return ([F(1, 48), F(23, 48), F(23, 48), F(1, 48)], [F(-1, 8), F(-5, 8), F(5, 8), F(1, 8)],
+            [F(1, 2), F(-1, 2), F(-1, 2), F(1, 2)])
+
+
+def check_absmag_closed_forms(ev=oracle.eval_stencil):
+    """C_o for a table of ones on an orthorhombic cell with J = diag(1, 2, 2),
+    at offsets t_a in {0, 1/2}, against exact rational sums:
+    C_value = 1 (non-negative weights, partition of unity);
+    C_d/dx_a = J_aa sum_k |b'_k(t_a)| (the other two factors sum to 1);
+    C_lap = sum over the 64 sites of |sum_a J_aa^2 b''_a prod_{b != a} b_b|
+    (the absolute value of the combined weight, not of its three terms)."""
+    from fractions import Fraction as F
+    lat = np.diag([8.0, 6.0, 5.0])
+    grid = (8, 12, 10)
+    jd = [F(1), F(2), F(2)]                        # n_a / |a_a|
+    err = 0.0
+    for tt in ((0, 0, 0), (1, 1, 1), (0, 1, 0), (1, 0, 1)):
+        t = [F(k, 2) for k in tt]
+        g = [F(3) + t[0], F(5) + t[1], F(7) + t[2]]
+        pos = np.array([[float(g[a] / grid[a]) * lat[a, a] for a in range(3)]])
+        f = [_exact_1d(x) for x in t]
+        cv = F(0)
+        cl = F(0)
+        for kx, ky, kz in itertools.product(range(4), repeat=3):
+            k = (kx, ky, kz)
+            b = [f[a][0][k[a]] for a in range(3)]
+            cv += abs(b[0] * b[1] * b[2])
+            lap = F(0)
+            for a in range(3):
+                term = jd[a] ** 2 * f[a][2][k[a]]
+                for c in range(3):
+                    if c != a:
+                        term *= b[c]
+                lap += term
+            cl += abs(lap)
+        cg = [jd[a] * sum(abs(x) for x in f[a][1]) for a in range(3)]
+        for norm, s in ((0, 1.0), (1, 1.5 ** 3)):
+            _, _, _, mag = ev(grid, lat, np.ones(grid + (1,)), pos, norm=norm, absmag=True)
+            want = np.array([float(cv)] + [float(x) for x in cg] + [float(cl)]) * s
+            err = max(err, float(np.max(np.abs(mag[0, :, 0] - want) / want)))
+    return err

@@ -56,6 +56,30 @@ MUTANTS = [
     ("grid scale n missing from J",
      "J[3 * a + c] = (double)grid[a] * Ainv[3 * a + c];",
      "J[3 * a + c] = (double)grid[c] * Ainv[3 * a + c];"),
+    # the rounding scale C_o = sum_s |W_o(s)| |a_ls| (absmag): an inflated
+    # scale would silently loosen every GPU parity bound built on it
+    ("absmag: gradient weights made absolute before the Jacobian contraction",
+     "double w = W[k], aw = fabs(W[k]);",
+     "double w = W[k], aw = (k >= 1 && k <= 3)\n"
+     "                        ? jb->norm * (fabs(jb->J[k - 1] * dg[0]) + fabs(jb->J[2 + k] * dg[1])\n"
+     "                                      + fabs(jb->J[5 + k] * dg[2]))\n"
+     "                        : fabs(W[k]);"),
+    ("absmag: Laplacian weight made absolute term by term",
+     "double w = W[k], aw = fabs(W[k]);",
+     "double aw = fabs(W[k]);\n"
+     "                    if (k == 4) {\n"
+     "                        aw = 0.0;\n"
+     "                        for (int a = 0; a < 3; ++a)\n"
+     "                            for (int b = 0; b < 3; ++b) aw += fabs(jb->M[3 * a + b] * hg[a][b]);\n"
+     "                        aw *= jb->norm;\n"
+     "                    }\n"
+     "                    double w = W[k];"),
+    ("absmag: factor 2 on the derivative kinds",
+     "double w = W[k], aw = fabs(W[k]);",
+     "double w = W[k], aw = (k ? 2.0 : 1.0) * fabs(W[k]);"),
+    ("absmag: signed coefficients",
+     "am[l] += aw * fabs(c[l]);",
+     "am[l] += aw * c[l];"),
 ]
 
 TOL = {
@@ -63,7 +87,8 @@ TOL = {
     "check_bspline_derivatives_fd": 1e-9, "check_partition_of_unity": 1e-13,
     "check_polynomial_reproduction": 1e-12, "check_plane_wave_nodes": 1e-12,
     "check_finite_differences": 1e-7, "check_vs_bruteforce": 1e-13,
-    "check_translation": 1e-12,
+    "check_translation": 1e-12, "check_absmag_vs_bruteforce": 1e-12,
+    "check_absmag_closed_forms": 1e-13,
 }
 
 

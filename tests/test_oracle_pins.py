@@ -48,6 +48,17 @@ def test_periodicity_and_grid_shift():
     assert pins.check_translation() < 1e-12
 
 
+def test_absmag_equals_bruteforce_sum_of_absolute_terms():
+    """The rounding scale C_o = sum_s |W_o(s)| |a_ls| of all five output
+    kinds (Eqs. 11.12.24.1, 11.12.24.2) against Oracle B's independent sum
+    over every (site, image) pair: pinned from above and below."""
+    assert pins.check_absmag_vs_bruteforce() < 1e-12
+
+
+def test_absmag_closed_forms_orthorhombic():
+    assert pins.check_absmag_closed_forms() < 1e-13
+
+
 def test_golden_bspline_table():
     """Exact rational values of B, B', B'' (tests/golden/bspline_values.txt)."""
     import os
