@@ -2,11 +2,18 @@
 """Benchmark: orbital x electron evaluations per second (value + gradient +
 Laplacian) of the periodic cubic-blip path on GB300.
 
-Default workload: the TiO2-shaped table (tetragonal 17.4 x 17.4 x 11.2 bohr,
-72 x 72 x 48 grid, 768 real orbitals, FP32 storage) evaluated at 1,536
-uniform positions all at once (one batched launch per step).  A step is one
+Default workload: the quasi-simultaneous precision batch on the TiO2-shaped
+table (tetragonal 17.4 x 17.4 x 11.2 bohr, 72 x 72 x 48 grid, 768 real
+orbitals): 1,024 walkers x 1,536 trial moves (Gaussian, sigma 0.3 bohr) in
+one launch per step, FP32 storage for the headline value.  A step is one
 blip_eval of the batch; L2 is flushed (512 MB write, then 512 MB read so no
 dirty lines remain) between steps outside the per-step CUDA-event window.
+Beside it the line carries BF16 and FP16 storage on the same positions
+(throughput, error against the FP64 oracle on sampled electrons, and the
+Slater-only kinetic-energy error per primitive cell of two walkers), the
+values-only and fused-ratio paths, the batch sweep of 256 walkers x
+b in {1, 8, 32, 128, 1536} for FP32 and BF16, and the 1,536-electron
+single-walker launch (all at once and one electron per launch).
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores on the same workload instead.
@@ -47,7 +54,12 @@ NCU_TRAFFIC = {
     ("33f210082c611060", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156558592 + 947191552)},
 }
 
+# the metric and its unit, identical in every arm of the benchmark
+METRIC = "orbital\u00b7electron evals/s (val+grad+lap), % HBM roofline; BF16 vs FP32 at err"
+UNIT = "orbital*electron evals/s (val+grad+lap)"
+
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "c64": 3, "bf16pair": 4}
+DTYPE = {"f32": "f32", "bf16": "bf16", "f16": "f16", "c64": "f32", "bf16pair": "bf16"}
 ELEM_BYTES = {"f32": 4, "bf16": 2, "f16": 2, "c64": 4, "bf16pair": 2}   # per real component
 
 
@@ -57,7 +69,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tio2",
+    ap.add_argument("--workload", default="tio2_precision",
                     choices=["tio2", "tio2_batch", "tio2_precision", "cubic16",
                              "tio2_super_complex", "sm_update"])
     ap.add_argument("--batch", type=int, default=1536, help="electrons per walker (tio2_batch)")
@@ -74,6 +86,8 @@ def parse():
     ap.add_argument("--warm", action="store_true",
                     help="no L2 flush between steps (tables that fit in L2)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--sweep", default="1,8,32,128,1536",
+                    help="batch sizes of the 256-walker sweep extra ('' for none)")
     return ap.parse_args()
 
 
@@ -258,7 +272,7 @@ def cpu_baseline(w, tab, pos, seconds):
     t1 = time.perf_counter()
     oracle.eval_stencil(w.grid, w.lattice, tab, pos[:n1], threads=1)
     dt1 = time.perf_counter() - t1
-    return {"value": n * reps * Lr / dt, "unit": "orbital*electron evals/s (val+grad+lap)",
+    return {"value": n * reps * Lr / dt, "unit": UNIT,
             "cores": cores, "kind": "oracle",
             "sample": f"first {n} of {E} positions x {reps} repeats, FP64, {cores} threads, "
                       f"{dt:.1f} s",
@@ -279,11 +293,11 @@ def run_reference(args):
     pos, offs = w.positions()
     cores = os.cpu_count() or 1
     E = len(pos)
-    # bound each step to about 2 s of wall time
+    # bound each step to about 1.5 s of wall time
     t0 = time.perf_counter()
     oracle.eval_stencil(w.grid, w.lattice, tab, pos[: min(E, 256)], threads=cores)
     per_e = (time.perf_counter() - t0) / min(E, 256)
-    n = int(max(16, min(E, 2.0 / max(per_e, 1e-9))))
+    n = int(max(16, min(E, 1.5 / max(per_e, 1e-9))))
     for _ in range(args.warmup):
         oracle.eval_stencil(w.grid, w.lattice, tab, pos[:n], threads=cores)
     times = []
@@ -293,8 +307,8 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
     value = n * w.n_orb / (ms / 1e3)
-    unit = "orbital*electron evals/s (val+grad+lap)"
-    line = {"impl": "reference", "metric": "orbital*electron evals/s (val+grad+lap)",
+    unit = UNIT
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -359,6 +373,128 @@ def run_sm(args):
     return 0
 
 
+class Stepper:
+    """Timing of repeated launches: L2 flush between launches (512 MB
+    written, then 512 MB read, so no dirty lines are charged to the next
+    launch), a device-side hold so that the host enqueues every launch
+    before the first one starts, CUDA events around each launch on the
+    launching stream."""
+
+    def __init__(self, warm_l2, stream):
+        import torch
+        self.torch = torch
+        self.warm = warm_l2
+        self.stream = stream
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        self.flush_rd = torch.ones(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2(self, k):
+        if self.warm:                  # warm L2: the table stays cached between steps
+            return
+        self.flush.fill_(float(k))
+        self.flush_rd.sum()
+
+    def hold(self, steps, per_step_s=0.002):
+        # a device-side wait (torch's spin kernel) ahead of timed launches:
+        # the host enqueues them all while it runs, so a host stall cannot
+        # leave the GPU idle inside a step's CUDA-event window; it runs
+        # before the first event, outside every window
+        sleep = getattr(self.torch.cuda, "_sleep", None)
+        if sleep is not None:
+            sleep(int(2.0e9 * (0.05 + per_step_s * steps)))
+
+    def time(self, fn, K, warmup=3):
+        """Per-launch times (ms) of K launches of fn()."""
+        torch = self.torch
+        for k in range(warmup):
+            self.flush_l2(k)
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+        torch.cuda.synchronize()
+        self.hold(K)
+        for k in range(K):
+            self.flush_l2(k)
+            evs[k][0].record(self.stream)
+            fn()
+            evs[k][1].record(self.stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+
+def launch_model(mode, E, Lr, U, b_c):
+    """Algorithmic bytes and FP32 FLOPs of one launch.  mode: 'full' (value,
+    gradient, Laplacian: 20 L B and 640 FLOP per eval), 'vonly' (4 L B, 128
+    FLOP), 'ratio' (the inverse columns read, 4 L B, five floats written per
+    electron, 650 FLOP per eval).  Table bytes: the U touched rows once."""
+    out = {"full": 20.0 * Lr * E, "vonly": 4.0 * Lr * E,
+           "ratio": 4.0 * Lr * E + 20.0 * E}[mode]
+    fl = {"full": 640.0, "vonly": 128.0, "ratio": 650.0}[mode] * Lr * E
+    return U * Lr * b_c + out + 24.0 * E, fl
+
+
+def roofline(bytes_alg, flops, ms, sms):
+    """The binding roofline of one launch: HBM (measured copy bandwidth) or
+    the FP32 FMA pipe (SMs x 128 lanes x 2 FLOP x 2.07 GHz)."""
+    peak, peak_kind = measured_peaks()
+    f32_peak = sms * 128 * 2 * 2.07e9 / 1e12
+    t_hbm = bytes_alg / (peak * 1e9)
+    t_alu = flops / (f32_peak * 1e12)
+    hbm_ach = bytes_alg / (ms / 1e3) / 1e9
+    alu_ach = flops / (ms / 1e3) / 1e12
+    if t_hbm >= t_alu:
+        r = {"bound": "hbm", "achieved": hbm_ach, "peak": peak, "unit": "GB/s",
+             "frac": hbm_ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
+    else:
+        r = {"bound": "alu", "achieved": alu_ach, "peak": f32_peak, "unit": "TFLOP/s",
+             "frac": alu_ach / f32_peak,
+             "peak_kind": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x 2.07 GHz"}
+    r.update({"algorithmic_bytes_per_launch": bytes_alg, "fp32_flop_per_launch": flops,
+              "hbm_frac": hbm_ach / peak, "alu_frac": alu_ach / f32_peak,
+              "roof_time_us": 1e6 * max(t_hbm, t_alu)})
+    return r
+
+
+def sample_idx(n, k, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, size=k)]))
+
+
+def error_stats(w, tab, pos, idx, rows):
+    """Max and RMS error of GPU outputs ``rows`` (values, grads, laps at
+    electrons idx) against the FP64 oracle, absolute and relative to the
+    rounding scale C_o = sum_s |W_o(s)| |a_ls|."""
+    import oracle
+    v, g, lp, mag = oracle.eval_stencil(w.grid, w.lattice, tab, pos[idx], absmag=True)
+    refs = [v, g, lp]
+    mags = [mag[:, 0], mag[:, 1:4], mag[:, 4]]
+    out = {}
+    for name, got, ref, m in zip(("value", "grad", "lap"), rows, refs, mags):
+        err = np.abs(np.asarray(got, dtype=np.float64) - ref)
+        out[name] = {"max_abs": float(err.max()), "rms_abs": float(np.sqrt(np.mean(err ** 2))),
+                     "max_rel_to_C": float((err / (m + 1e-300)).max()),
+                     "ref_rms": float(np.sqrt(np.mean(ref ** 2)))}
+    return out
+
+
+def kinetic_errors(w, tab, pos, vals, laps, n_walk=2, per=1536):
+    """|T_L(gpu) - T_L(oracle)| / 64 per walker (Slater-only local kinetic
+    energy, two spins of per/2 electrons, 64 primitive cells per walker)."""
+    import oracle
+    h = per // 2
+    blocks = [(0, h), (h, per)]
+    out = []
+    for wk in range(n_walk):
+        p0 = pos[per * wk:per * (wk + 1)]
+        rv, _, rl = oracle.eval_stencil(w.grid, w.lattice, tab, p0)
+        T_ref, conds = oracle.kinetic.local_kinetic(rv, rl, blocks)
+        T_gpu, _ = oracle.kinetic.local_kinetic(vals[per * wk:per * (wk + 1)],
+                                                laps[per * wk:per * (wk + 1)], blocks)
+        out.append({"T_ref": T_ref, "err_per_cell": abs(T_gpu - T_ref) / 64.0,
+                    "cond": max(conds)})
+    return out
+
+
 def main():
     args = parse()
     if args.workload == "sm_update":
@@ -391,6 +527,8 @@ def main():
         tab = None
         torch.cuda.empty_cache()
     info = t.info()
+    sms = info["sm_count"]
+    Lr = info["Lreal"]
     dpos = torch.from_numpy(pos).cuda()
     doffs = torch.from_numpy(offs).cuda()
     out = t.alloc_outputs(E)
@@ -401,31 +539,13 @@ def main():
         v_, c_, w_, s_ = (int(x) for x in args.kernel.split(","))
         t.set_kernel(v_, c_, w_, s_)
         chosen = (v_, c_, w_, s_)
-    # L2 flush between steps: write 512 MB, then read another 512 MB so the
-    # L2 is left holding clean lines (no write-back charged to the next step)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    flush_rd = torch.ones(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def flush_l2(k):
-        if args.warm:                  # warm L2: the table stays cached between steps
-            return None
-        flush.fill_(float(k))
-        return flush_rd.sum()
+    st_ = Stepper(args.warm, stream)
 
     def step():
         t.eval(dpos, doffs, out=out)
 
-    def hold_queue(steps):
-        # a device-side wait (torch's spin kernel, 50 ms + 2 ms per step)
-        # ahead of timed launches: the host enqueues them all while it runs,
-        # so a host stall cannot leave the GPU idle inside a step's CUDA-event
-        # window; it runs before the first event, outside every window
-        sleep = getattr(torch.cuda, "_sleep", None)
-        if sleep is not None:
-            sleep(int(2.0e9 * (0.05 + 0.002 * steps)))
-
     for k in range(max(3, args.warmup)):
-        flush_l2(k)
+        st_.flush_l2(k)
         step()
     torch.cuda.synchronize()
     st = t.status()
@@ -440,9 +560,9 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    hold_queue(K)
+    st_.hold(K)
     for k in range(K):
-        flush_l2(k)
+        st_.flush_l2(k)
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
@@ -457,126 +577,68 @@ def main():
     evals = E * w.n_orb
     value = world * evals / (ms / 1e3)
 
-    # roofline of the evaluation kernel (the only kernel in the step)
+    # roofline of the evaluation kernel (the dominant kernel of the step)
     U = touched_sites(w.grid, w.lattice, pos)
-    Lr = info["Lreal"]
-    bytes_alg = U * Lr * ELEM_BYTES[args.storage] + 20 * Lr * E + 24 * E
-    peak, peak_kind = measured_peaks()
+    b_c = ELEM_BYTES[args.storage]
+    bytes_alg, flops = launch_model("full", E, Lr, U, b_c)
+    roof = roofline(bytes_alg, flops, ms, sms)
     kh = kernel_hash()
-    rec = NCU_TRAFFIC.get((kh, w.name, args.storage, E), {}).get(tuple(chosen[:2]))
-    # FP32 FMA peak from unit counts and clock: SMs x 128 FP32 lanes x 2 FLOP
-    # x 2.07 GHz (maximum SM clock)
-    sms = info["sm_count"]
-    f32_peak = sms * 128 * 2 * 2.07e9 / 1e12
-    flops = 640.0 * Lr * E
-    t_hbm = bytes_alg / (peak * 1e9)
-    t_alu = flops / (f32_peak * 1e12)
-    hbm_ach = bytes_alg / (ms / 1e3) / 1e9
-    alu_ach = flops / (ms / 1e3) / 1e12
-    if t_hbm >= t_alu:
-        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": peak, "unit": "GB/s",
-                "frac": hbm_ach / peak, "traffic": rec,
-                "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
-    else:
-        roof = {"bound": "alu", "achieved": alu_ach, "peak": f32_peak, "unit": "TFLOP/s",
-                "frac": alu_ach / f32_peak, "traffic": rec,
-                "peak_kind": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x 2.07 GHz"}
-        if not args.no_probe:
-            sg = sgemm_tflops()
-            roof["fp32_sgemm_tflops"] = sg
-            roof["frac_of_sgemm"] = alu_ach / sg
-    roof.update({"algorithmic_bytes_per_launch": bytes_alg, "touched_sites": U,
-                 "fp32_flop_per_launch": flops, "kernel_source_hash": kh,
-                 "hbm_frac": hbm_ach / peak, "alu_frac": alu_ach / f32_peak,
-                 "roof_time_us": 1e6 * max(t_hbm, t_alu),
-                 "gather_model_GBps": (E * 64 * Lr * ELEM_BYTES[args.storage] + 20 * Lr * E)
-                                      / (ms / 1e3) / 1e9})
+    roof["traffic"] = NCU_TRAFFIC.get((kh, w.name, args.storage, E), {}).get(tuple(chosen[:2]))
+    roof.update({"touched_sites": U, "kernel_source_hash": kh,
+                 "gather_model_GBps": (E * 64 * Lr * b_c + 20 * Lr * E) / (ms / 1e3) / 1e9})
+    if roof["bound"] == "alu" and not args.no_probe:
+        sg = sgemm_tflops()
+        roof["fp32_sgemm_tflops"] = sg
+        roof["frac_of_sgemm"] = roof["achieved"] / sg
+    if roof["bound"] == "alu" and clocks and clocks.get("sm_mhz"):
+        # the same fraction at the SM clock sampled during the timed region
+        roof["frac_at_sampled_clock"] = roof["frac"] * 2070.0 / clocks["sm_mhz"]
 
-    line = {"metric": "orbital*electron evals/s (val+grad+lap)", "value": value,
-            "unit": "orbital*electron evals/s", "n_gpus": world, "steps": K,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "ms_median": ms_median,
-            "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.storage], "data": "synthetic",
             "config": describe(w, args, E), "roofline": roof, "clocks": clocks,
             "gpu_launches": K * (6 if chosen[3] else 1), "kernel_choice": list(chosen),
-            "status": st,
-            "wall_s_timed_region": wall}
-
-    if not args.no_probe and args.storage in ("f32", "c64") and chosen[3] == 0:
-        # the access pattern's own time (blip_probe_gather): the evaluation's
-        # item walk, FP64 geometry, row loads and output stores without the
-        # weights and FMAs, timed like the steps above (the probe walks the
-        # batch in input order, so it is the ceiling of unsorted launches)
-        def probe_ms(store):
-            for k in range(3):
-                flush_l2(k)
-                t.probe_gather(dpos, out=out, store=store)
-            pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(K)]
-            hold_queue(K)
-            for k in range(K):
-                flush_l2(k)
-                pe[k][0].record(stream)
-                t.probe_gather(dpos, out=out, store=store)
-                pe[k][1].record(stream)
-            torch.cuda.synchronize()
-            return statistics.mean(a.elapsed_time(b) for a, b in pe)
-        g_ms, gs_ms = probe_ms(False), probe_ms(True)
-        line["pattern_ceiling"] = {
-            "gather_us": 1e3 * g_ms, "gather_store_us": 1e3 * gs_ms, "kernel_us": 1e3 * ms,
-            "kernel_frac_of_ceiling": gs_ms / ms,
-            "ceiling_frac_of_copy": bytes_alg / (gs_ms / 1e3) / 1e9 / peak,
-            "what": "blip_probe_gather on the same positions (input order): geometry, the 64 row "
-                    "loads per item and (gather_store) the output stores, without the arithmetic"}
+            "status": st, "wall_s_timed_region": wall}
 
     if not args.no_e2e:
-        # end to end through the host-buffer entry point: H2D positions,
-        # evaluation, D2H of all outputs, per step
-        hp = torch.from_numpy(pos).pin_memory()
-        ho = torch.from_numpy(offs).pin_memory()
-        hv = torch.empty((E, Lr), dtype=torch.float32).pin_memory()
-        hg = torch.empty((E, 3, Lr), dtype=torch.float32).pin_memory()
-        hl = torch.empty((E, Lr), dtype=torch.float32).pin_memory()
-        for _ in range(2):
-            t.eval_host(hp, ho, out=(hv, hg, hl))
-        tt = []
-        for _ in range(K):
-            t0 = time.perf_counter()
-            t.eval_host(hp, ho, out=(hv, hg, hl))
-            tt.append(time.perf_counter() - t0)
-        e_ms = replicas.max_over_ranks(1e3 * statistics.mean(tt))
-        line["e2e"] = {"value": world * evals / (e_ms / 1e3), "unit": "orbital*electron evals/s",
-                       "h2d_bytes_per_step": int(hp.numel() * 8 + ho.numel() * 4),
-                       "d2h_bytes_per_step": int((hv.numel() + hg.numel() + hl.numel()) * 4),
-                       "ms_per_step": e_ms,
-                       "api": "blip_eval_host with page-locked host buffers (the kernel reads the "
-                              "positions and writes the outputs across the host link)"}
+        # end to end through the host-buffer entry point: positions from
+        # page-locked host memory, evaluation, all outputs back to page-locked
+        # host memory, every step (blip_eval_host)
+        try:
+            hp = torch.from_numpy(pos).pin_memory()
+            ho = torch.from_numpy(offs).pin_memory()
+            hv = torch.empty((E, Lr), dtype=torch.float32).pin_memory()
+            hg = torch.empty((E, 3, Lr), dtype=torch.float32).pin_memory()
+            hl = torch.empty((E, Lr), dtype=torch.float32).pin_memory()
+            for _ in range(2):
+                t.eval_host(hp, ho, out=(hv, hg, hl))
+            tt = []
+            for _ in range(K):
+                t0 = time.perf_counter()
+                t.eval_host(hp, ho, out=(hv, hg, hl))
+                tt.append(time.perf_counter() - t0)
+            e_ms = replicas.max_over_ranks(1e3 * statistics.mean(tt))
+            line["e2e"] = {"value": world * evals / (e_ms / 1e3), "unit": UNIT,
+                           "h2d_bytes_per_step": int(hp.numel() * 8 + ho.numel() * 4),
+                           "d2h_bytes_per_step": int((hv.numel() + hg.numel() + hl.numel()) * 4),
+                           "ms_per_step": e_ms,
+                           "api": "blip_eval_host with page-locked host buffers (the kernel "
+                                  "reads the positions and writes the outputs across the "
+                                  "host link)"}
+            del hv, hg, hl
+        except RuntimeError as ex:      # host memory: state it in the line
+            line["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None,
+                           "d2h_bytes_per_step": None,
+                           "unavailable": f"page-locked host buffers of the full outputs "
+                                          f"({20 * E * Lr / 1e9:.1f} GB): {str(ex)[:120]}"}
 
-    if not args.no_extra and args.workload == "tio2" and rank == 0:
-        # one electron per launch (particle-by-particle order), 1,536 kernel
-        # nodes in one CUDA graph
-        o1 = t.alloc_outputs(E)
-        one_choice = list(chosen)
-        if args.kernel == "auto":      # tune the one-electron launch too
-            one_choice = list(t.autotune(dpos[:1].contiguous(), out=tuple(x[:1] for x in o1)))
-        g = t.graph(dpos, o1, 1)
-        for _ in range(2):
-            g.launch()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 5
-        hold_queue(reps)
-        a.record(stream)
-        for _ in range(reps):
-            g.launch()
-        b.record(stream)
-        torch.cuda.synchronize()
-        oms = a.elapsed_time(b) / reps
-        line["one_at_a_time"] = {"value": evals / (oms / 1e3), "ms_per_step": oms,
-                                 "us_per_electron": 1e3 * oms / E,
-                                 "how": "CUDA graph of 1,536 single-electron launches",
-                                 "kernel_choice": one_choice}
-        g.close()
+    if not args.no_extra and rank == 0 and tab is not None and w.name == "tio2_precision":
+        extras_precision(args, pb, w, tab, pos, dpos, doffs, t, out, st_, line, sms, chosen, ms)
+    if not args.no_extra and rank == 0 and tab is not None and w.name in ("tio2_precision",
+                                                                           "tio2"):
+        extras_single_walker(args, pb, w, tab, t, st_, line, sms, stream)
 
     if w.is_complex:
         line["real_equivalent_value"] = 2 * value
@@ -589,6 +651,160 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def _timed_entry(ms_list, E, Lr, U, b_c, mode, sms, chosen=None):
+    ms = statistics.mean(ms_list)
+    bytes_alg, flops = launch_model(mode, E, Lr, U, b_c)
+    r = roofline(bytes_alg, flops, ms, sms)
+    d = {"us": 1e3 * ms, "evals_per_s": E * Lr / (ms / 1e3), "bound": r["bound"],
+         "frac": r["frac"], "hbm_frac": r["hbm_frac"], "alu_frac": r["alu_frac"],
+         "roof_us": r["roof_time_us"]}
+    if chosen is not None:
+        d["kernel"] = list(chosen)
+    return d
+
+
+def extras_precision(args, pb, w, tab, pos, dpos, doffs, t32, out, st_, line, sms, chosen32,
+                     ms32):
+    """BF16 / FP16 storage on the same positions, errors against the FP64
+    oracle, kinetic-energy error per primitive cell, values-only and fused
+    ratio paths, and the 256-walker batch sweep."""
+    import torch
+    E = len(pos)
+    K = args.steps
+    Lr = t32.info()["Lreal"]
+    U = line["roofline"]["touched_sites"]
+    idx = sample_idx(E, 62, 1)
+    prec = {}
+    tables = {"f32": t32}
+    for storage in ("f32", "bf16", "f16"):
+        if storage == "f32":
+            t = t32
+            ent = _timed_entry([ms32], E, Lr, U, 4, "full", sms, chosen32)
+        else:
+            t = pb.BlipTable(w.grid, w.lattice, tab, storage=STORAGE[storage])
+            ch = t.autotune(dpos, doffs, out=out)
+            ent = _timed_entry(st_.time(lambda: t.eval(dpos, doffs, out=out), K), E, Lr, U,
+                               ELEM_BYTES[storage], "full", sms, ch)
+            t.eval(dpos, doffs, out=out)
+            torch.cuda.synchronize()
+        rows = [out[0][idx].cpu().numpy(), out[1][idx].cpu().numpy(), out[2][idx].cpu().numpy()]
+        ent["errors"] = error_stats(w, tab, pos, idx, rows)
+        ent["errors"]["sample"] = f"{len(idx)} electrons (seeded) of {E}, all {Lr} orbitals"
+        ent["kinetic"] = kinetic_errors(w, tab, pos, out[0][:3072].cpu().numpy(),
+                                        out[2][:3072].cpu().numpy())
+        ent["status"] = t.status()
+        prec[storage] = ent
+        tables[storage] = t
+    prec["bf16_over_f32_throughput"] = prec["bf16"]["evals_per_s"] / prec["f32"]["evals_per_s"]
+    prec["f16_over_f32_throughput"] = prec["f16"]["evals_per_s"] / prec["f32"]["evals_per_s"]
+    prec["tolerance"] = ("paper: ~1e-3 hartree per primitive cell (64 cells per 1,536-electron "
+                         "walker); kinetic = Slater-only local kinetic energy of walkers 0, 1")
+    line["precision"] = prec
+    del tables["f16"]
+
+    # values only (the paper's GPU workload) and the fused ratio
+    vo = {}
+    for storage in ("f32", "bf16"):
+        t = tables[storage]
+        o1 = (out[0], None, None)
+        ch = t.autotune(dpos, doffs, values_only=True, out=o1)
+        vo[storage] = _timed_entry(st_.time(lambda: t.eval(dpos, doffs, values_only=True, out=o1),
+                                            K), E, Lr, U, ELEM_BYTES[storage], "vonly", sms, ch)
+    line["values_only"] = vo
+    cols = out[1].view(-1)[:E * Lr].view(E, Lr)          # any float data will do for timing
+    ra = {}
+    for storage in ("f32", "bf16"):
+        t = tables[storage]
+        best = None
+        for srt in (0, 1):
+            ms_l = st_.time(lambda: t.eval_ratio(dpos, cols, doffs, sort=srt), max(3, K // 4))
+            ent = _timed_entry(ms_l, E, Lr, U, ELEM_BYTES[storage], "ratio", sms)
+            ent["sort"] = srt
+            if best is None or ent["us"] < best["us"]:
+                best = ent
+        ra[storage] = best
+    line["ratio"] = ra
+
+    # 256 walkers x b electrons per walker per launch, FP32 and BF16
+    sweep = []
+    for b in [int(x) for x in args.sweep.split(",") if x.strip()]:
+        wb = bi.workload("tio2_batch", batch=b)
+        pb_, ob = wb.positions()
+        Eb = len(pb_)
+        db, dob = torch.from_numpy(pb_).cuda(), torch.from_numpy(ob).cuda()
+        ob_ = (out[0][:Eb], out[1][:Eb], out[2][:Eb])
+        Ub = touched_sites(wb.grid, wb.lattice, pb_)
+        for storage in ("f32", "bf16"):
+            t = tables[storage]
+            ch = t.autotune(db, dob, out=ob_)
+            ent = _timed_entry(st_.time(lambda: t.eval(db, dob, out=ob_), K), Eb, Lr, Ub,
+                               ELEM_BYTES[storage], "full", sms, ch)
+            ent.update({"b": b, "E": Eb, "storage": storage})
+            sweep.append(ent)
+    line["batch_sweep"] = sweep
+
+
+def extras_single_walker(args, pb, w, tab, t, st_, line, sms, stream):
+    """The 1,536-electron single walker (uniform positions) on the same FP32
+    table: all electrons in one launch (with the access-pattern probe), and
+    one electron per launch (a CUDA graph of 1,536 launches)."""
+    import torch
+    if w.name == "tio2":
+        w1, t1 = w, t
+    else:
+        w1 = bi.workload("tio2")
+        t1 = t if t.storage == 0 else pb.BlipTable(w1.grid, w1.lattice, tab, storage=0)
+    pos1, _ = w1.positions()
+    E = len(pos1)
+    K = args.steps
+    Lr = t1.info()["Lreal"]
+    d1 = torch.from_numpy(pos1).cuda()
+    o1 = t1.alloc_outputs(E)
+    ch = t1.autotune(d1, out=o1) if args.kernel == "auto" else tuple(
+        int(x) for x in args.kernel.split(","))
+    U1 = touched_sites(w1.grid, w1.lattice, pos1)
+    ms_l = st_.time(lambda: t1.eval(d1, out=o1), K)
+    ent = _timed_entry(ms_l, E, Lr, U1, 4, "full", sms, ch)
+    ms = statistics.mean(ms_l)
+    if not args.no_probe and ch[3] == 0:
+        # the access pattern's own time (blip_probe_gather): the evaluation's
+        # item walk, FP64 geometry, row loads and output stores without the
+        # weights and FMAs (input order: the ceiling of unsorted launches)
+        g_ms = statistics.mean(st_.time(lambda: t1.probe_gather(d1, out=o1, store=False), K))
+        gs_ms = statistics.mean(st_.time(lambda: t1.probe_gather(d1, out=o1, store=True), K))
+        bytes_alg, _ = launch_model("full", E, Lr, U1, 4)
+        peak, _ = measured_peaks()
+        ent["pattern_ceiling"] = {
+            "gather_us": 1e3 * g_ms, "gather_store_us": 1e3 * gs_ms,
+            "kernel_frac_of_ceiling": gs_ms / ms,
+            "ceiling_frac_of_copy": bytes_alg / (gs_ms / 1e3) / 1e9 / peak}
+    # one electron per launch (particle-by-particle order), 1,536 kernel
+    # nodes in one CUDA graph
+    one_choice = list(ch)
+    if args.kernel == "auto":
+        one_choice = list(t1.autotune(d1[:1].contiguous(), out=tuple(x[:1] for x in o1)))
+    g = t1.graph(d1, o1, 1)
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    st_.hold(reps, per_step_s=0.01)
+    a.record(stream)
+    for _ in range(reps):
+        g.launch()
+    b.record(stream)
+    torch.cuda.synchronize()
+    oms = a.elapsed_time(b) / reps
+    ent["one_at_a_time"] = {"evals_per_s": E * w1.n_orb / (oms / 1e3), "ms_per_step": oms,
+                            "us_per_electron": 1e3 * oms / E,
+                            "how": "CUDA graph of 1,536 single-electron launches",
+                            "kernel": one_choice}
+    g.close()
+    ent["workload"] = "tio2: 1 walker, 1,536 uniform positions, FP32"
+    line["single_walker"] = ent
 
 
 if __name__ == "__main__":

@@ -246,11 +246,16 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort);
 
 /*
  * blip_autotune - time each kernel configuration on this batch shape and keep
- * the fastest for batches of this size class (median of 7 runs, then of 15
- * more for the configurations within 5 % of the best; each run after a read
- * sweep of a 256 MB scratch that leaves only its clean lines in L2; the
- * scratch is allocated for the call).  Same arguments as blip_eval (the outputs are overwritten).
- * Synchronises the stream; must not be called during stream capture.  *chosen receives {variant, chunks, warps, sort}.
+ * the fastest for batches of this size class (the bit length of n_elec) and
+ * output mode (values only, or all five outputs).  Every candidate is timed
+ * once; the 12 fastest, median of 7 runs; those within 5 % of the best
+ * median, 15 more runs each, interleaved; of these the earliest in the
+ * candidate list whose median is within 1 % of the best is kept (a stable
+ * choice when the gap is below the timing noise).  Each run follows a read
+ * sweep of a 256 MB scratch that leaves only its clean lines in L2 (the
+ * scratch is allocated for the call).  Same arguments as blip_eval (the
+ * outputs are overwritten).  Synchronises the stream; must not be called
+ * during stream capture.  *chosen receives {variant, chunks, warps, sort}.
  */
 int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
                   int n_walkers, void *values, void *grads, void *laps, void *stream,
@@ -339,6 +344,17 @@ int blip_sm_update(int n_walkers, int n, float *dinv, const float *rows, const i
 int blip_test_stall_pipeline(blip_table t, int on);
 
 /*
+ * blip_test_fail_alloc - test hook for the out-of-memory path (no
+ * counterpart in the paper).  With n >= 0 the library's device allocations
+ * succeed n more times and the next one fails with cudaErrorMemoryAllocation
+ * without calling cudaMalloc; the entry point that asked for it returns
+ * BLIP_ERR_OOM after releasing what it had allocated (blip_create leaves
+ * *out NULL), and the hook disarms itself.  n < 0 disarms it.  The setting
+ * is process-wide.  Nothing is allocated, faulted or left in a bad state.
+ */
+int blip_test_fail_alloc(int n);
+
+/*
  * blip_graph_create - capture a fixed evaluation into a CUDA graph.
  * The graph evaluates pos[0 .. n_elec) with the given buffers in launches of
  * per_launch electrons each (per_launch = 1 reproduces one-at-a-time,
@@ -371,9 +387,10 @@ int blip_graph_destroy(blip_graph g);
  * evaluation kernel is the table's current choice (blip_set_kernel /
  * blip_autotune), always run on the cell-sorted order.
  * Limit: the scratch needed is about 4 (n1' n2' n3 + 1) + 8 n_elec bytes,
- * with n1', n2' the grid sizes rounded up to multiples of 8; a batch that
- * needs more than 8 MiB returns BLIP_ERR_SCRATCH_LIMIT and does nothing
- * (about 0.9 million electrons on the 72 x 72 x 48 grid).
+ * with n1', n2' the grid sizes rounded up to multiples of 32 (the sort's
+ * 32 x 32-column super-bricks); a batch that needs more than 8 MiB returns
+ * BLIP_ERR_SCRATCH_LIMIT and does nothing (about 0.8 million electrons on the
+ * 72 x 72 x 48 grid).
  * The table's device must be the current device.  The first call on a device
  * looks up the buffer's device address (which may load the library's code on
  * that device); make that first call before any stream capture.

@@ -48,6 +48,7 @@ EXPORTED = {
     "blip_set_kpoints": (I, [P, I, P, P]),
     "blip_sm_update": (I, [I, I, P, P, P, P, P]),
     "blip_test_stall_pipeline": (I, [P, I]),
+    "blip_test_fail_alloc": (I, [I]),
     "blip_probe_gather": (I, [P, P, I, P, P, P, I, P]),
 }
 

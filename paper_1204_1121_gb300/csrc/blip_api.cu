@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <new>
@@ -43,7 +44,7 @@ struct blip_table_s {
     Geometry geo{};
     KernelChoice choice{VAR_REGISTER, 1, 8, 0};
     bool auto_mode = false;
-    std::map<int, KernelChoice> tuned;   // by batch size class (bit length of n_elec)
+    std::map<int, KernelChoice> tuned;   // by tune_key (batch size class, values-only mode)
     cudaStream_t last_stream = nullptr;
     bool used = false;
     // host-buffer entry point staging
@@ -72,6 +73,30 @@ struct blip_graph_s {
 };
 
 namespace {
+
+// Test hook (blip_test_fail_alloc): while >= 0, the number of library device
+// allocations that still succeed before one fails.
+std::atomic<int> g_alloc_fail_after{-1};
+
+// Every device allocation of the library goes through here.
+template <typename T>
+cudaError_t dev_alloc(T **p, size_t bytes)
+{
+    int n = g_alloc_fail_after.load();
+    while (n >= 0) {
+        if (g_alloc_fail_after.compare_exchange_weak(n, n - 1)) {
+            if (n == 0) {                  // the injected failure; the hook disarms
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    void *v = nullptr;
+    const cudaError_t e = cudaMalloc(&v, bytes);
+    *p = static_cast<T *>(v);
+    return e;
+}
 
 int cuda_fail(cudaError_t e)
 {
@@ -155,10 +180,14 @@ int size_class(int n_elec)
     return c;
 }
 
-KernelChoice pick(const blip_table_s *t, int n_elec)
+// Key of the tuned choices: batch size class and output mode (values only or
+// all five outputs), which load the kernels differently.
+int tune_key(int n_elec, bool values_only) { return 2 * size_class(n_elec) + (values_only ? 1 : 0); }
+
+KernelChoice pick(const blip_table_s *t, int n_elec, bool values_only)
 {
     if (t->auto_mode) {
-        auto it = t->tuned.find(size_class(n_elec));
+        auto it = t->tuned.find(tune_key(n_elec, values_only));
         if (it != t->tuned.end()) return it->second;
     }
     return t->choice;
@@ -194,7 +223,7 @@ int sorted_order(blip_table_s *t, const double *pos, int n_elec, cudaStream_t st
         }
         t->scratch = nullptr;
         t->scratch_bytes = 0;
-        CK(cudaMalloc(&t->scratch, need));
+        CK(dev_alloc(&t->scratch, need));
         t->scratch_bytes = need;
     }
     if (georec) {
@@ -322,7 +351,7 @@ int grow_stage(blip_table_s *t, size_t bytes)
     if (t->stage) cudaFree(t->stage);
     t->stage = nullptr;
     t->stage_bytes = 0;
-    CK(cudaMalloc(&t->stage, bytes));
+    CK(dev_alloc(&t->stage, bytes));
     t->stage_bytes = bytes;
     return BLIP_OK;
 }
@@ -385,13 +414,13 @@ int create_impl(const int grid[3], const double lattice[9], int n_orb, int stora
     // any stream (the library's stream does not order after the legacy
     // default stream): wait for the whole device before reading it.
     if (coeffs_on_device) CK(cudaDeviceSynchronize());
-    CK(cudaMalloc(&t->d_status, sizeof(int)));
+    CK(dev_alloc(&t->d_status, sizeof(int)));
     CK(cudaMemsetAsync(t->d_status, 0, sizeof(int), s));
 
     // 1. FP32 table in the ghost-plane layout
     const size_t f32_bytes = (size_t)t->rows * t->row_stride * sizeof(float);
     float *f32 = nullptr;
-    CK(cudaMalloc(&f32, f32_bytes));
+    CK(dev_alloc(&f32, f32_bytes));
     const size_t esz = coeffs_is_double ? 8 : 4;
     const size_t src_row_bytes = (size_t)t->Lreal * esz;
     if (coeffs_on_device) {
@@ -403,7 +432,7 @@ int create_impl(const int grid[3], const double lattice[9], int n_orb, int stora
         long long slab = std::max<long long>(1, (64LL << 20) / (long long)src_row_bytes);
         slab = std::min(slab, src_rows);
         void *tmp = nullptr;
-        cudaError_t e = cudaMalloc(&tmp, (size_t)slab * src_row_bytes);
+        cudaError_t e = dev_alloc(&tmp, (size_t)slab * src_row_bytes);
         if (e != cudaSuccess) { cudaFree(f32); return cuda_fail(e); }
         for (long long r0 = 0; r0 < src_rows && e == cudaSuccess; r0 += slab) {
             const long long nr = std::min(slab, src_rows - r0);
@@ -425,16 +454,16 @@ int create_impl(const int grid[3], const double lattice[9], int n_orb, int stora
         // 2. per-component scales, then quantise
         std::vector<float> ones((size_t)t->row_stride, 1.0f);
         unsigned int *bits = nullptr;
-        cudaError_t e = cudaMalloc(&t->d_scales, sizeof(float) * (size_t)t->row_stride);
+        cudaError_t e = dev_alloc(&t->d_scales, sizeof(float) * (size_t)t->row_stride);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(t->d_scales, ones.data(), sizeof(float) * ones.size(),
                                 cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMalloc(&bits, sizeof(unsigned int) * (size_t)t->Lreal);
+        if (e == cudaSuccess) e = dev_alloc(&bits, sizeof(unsigned int) * (size_t)t->Lreal);
         if (e == cudaSuccess) e = launch_absmax(f32, t->rows, t->row_stride, t->Lreal, bits, s);
         if (e == cudaSuccess)
             e = launch_make_scales(bits, t->Lreal, t->is_complex ? 1 : 0, t->d_scales, s);
         const size_t qbytes = (size_t)t->rows * t->row_stride * 2;
-        if (e == cudaSuccess) e = cudaMalloc(&t->d_table, qbytes);
+        if (e == cudaSuccess) e = dev_alloc(&t->d_table, qbytes);
         if (e == cudaSuccess)
             e = launch_quantize(f32, t->rows, t->row_stride, t->Lreal, t->d_scales, t->elem,
                                 t->d_table, s);
@@ -512,7 +541,7 @@ int blip_eval(blip_table t, const double *pos, int n_elec, const int *walker_off
     int rc = validate_eval(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps);
     if (rc) return rc;
     return eval_device(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps,
-                       static_cast<cudaStream_t>(stream), pick(t, n_elec));
+                       static_cast<cudaStream_t>(stream), pick(t, n_elec, grads == nullptr));
 }
 
 int blip_probe_gather(blip_table t, const double *pos, int n_elec, void *values, void *grads,
@@ -562,7 +591,7 @@ int blip_eval_host(blip_table t, const double *pos, int n_elec, const int *walke
         if (dp && dv && (!grads || (dg && dl)) && (!walker_offsets || doff)) {
             rc = eval_device(t, static_cast<const double *>(dp), n_elec,
                              static_cast<const int *>(doff), n_walkers, dv, dg, dl,
-                             t->own_stream, pick(t, n_elec));
+                             t->own_stream, pick(t, n_elec, grads == nullptr));
             if (rc) return rc;
             CK(cudaStreamSynchronize(t->own_stream));
             return BLIP_OK;
@@ -585,7 +614,8 @@ int blip_eval_host(blip_table t, const double *pos, int n_elec, const int *walke
     cudaStream_t s = t->own_stream;
     CK(cudaMemcpyAsync(d_pos, pos, pos_b, cudaMemcpyHostToDevice, s));
     if (d_off) CK(cudaMemcpyAsync(d_off, walker_offsets, off_b, cudaMemcpyHostToDevice, s));
-    rc = eval_device(t, d_pos, n_elec, d_off, n_walkers, d_val, d_grd, d_lap, s, pick(t, n_elec));
+    rc = eval_device(t, d_pos, n_elec, d_off, n_walkers, d_val, d_grd, d_lap, s,
+                     pick(t, n_elec, grads == nullptr));
     if (rc) return rc;
     CK(cudaMemcpyAsync(values, d_val, val_b, cudaMemcpyDeviceToHost, s));
     if (grads) {
@@ -694,13 +724,14 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
                 cands.push_back(KernelChoice{VAR_REGISTER_PIPE, c, w, srt});
                 cands.push_back(KernelChoice{VAR_REGISTER_ROLLED, c, w, srt});
                 if (c == 1 && t->elem == ELEM_F32) {
-                    cands.push_back(KernelChoice{VAR_REGISTER_PIPE3, c, w, srt});
-                    if (srt && t->nchunk > c) cands.push_back(KernelChoice{VAR_REGISTER_PIPE3, c, w, 2});
+                    // the persistent form first: near-ties go to it
                     if (!t->n_k) {
                         cands.push_back(KernelChoice{VAR_REGISTER_PERSIST, c, w, srt});
                         if (srt && t->nchunk > c)
                             cands.push_back(KernelChoice{VAR_REGISTER_PERSIST, c, w, 2});
                     }
+                    cands.push_back(KernelChoice{VAR_REGISTER_PIPE3, c, w, srt});
+                    if (srt && t->nchunk > c) cands.push_back(KernelChoice{VAR_REGISTER_PIPE3, c, w, 2});
                 }
                 if (srt && t->nchunk > c) {       // several chunk groups: try their order too
                     cands.push_back(KernelChoice{VAR_REGISTER, c, w, 2});
@@ -728,11 +759,15 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     // Each configuration is timed from a cold L2 (a read sweep of a 256 MB
     // scratch, twice the L2, before every run, outside the timed window, so
     // that L2 holds only clean lines), as it runs in a Monte Carlo step
-    // between other work: the median of 7 runs, then 15 more for the
-    // configurations within 5 % of the best.
+    // between other work.  Three passes: every candidate once (after one
+    // untimed run); the 12 fastest of those, median of 7 runs; the ones
+    // within 5 % of the best median (at most 4), 15 more runs each,
+    // interleaved.  The last pass keeps the earliest candidate of the list
+    // whose median is within 1 % of the best, so that configurations whose
+    // gap is below the timing noise do not trade places from run to run.
     void *flush = nullptr;
     const size_t flush_bytes = 256u << 20;
-    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    if (dev_alloc(&flush, flush_bytes) != cudaSuccess) {
         cudaGetLastError();
         flush = nullptr;                   // no room: time with a warm L2
     }
@@ -747,50 +782,69 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
         cudaEventElapsedTime(&ms, e0, e1);
         return r;
     };
-    // first pass: every candidate, median of 7 runs
-    std::vector<std::pair<float, KernelChoice>> med;
-    for (const KernelChoice &kc : cands) {
-        rc = eval_device(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps, s, kc);
-        if (rc) break;
-        float ts[7];
-        for (int rep = 0; rep < 7 && rc == 0; ++rep) rc = timed_run(kc, ts[rep]);
-        if (rc) break;
-        std::sort(ts, ts + 7);
-        med.push_back({ts[3], kc});
+    typedef std::pair<float, size_t> Timed;   // (ms, index into cands)
+    auto by_time = [](const Timed &a, const Timed &b) {
+        return a.first < b.first || (a.first == b.first && a.second < b.second);
+    };
+    // first pass: every candidate once
+    std::vector<Timed> once;
+    for (size_t i = 0; i < cands.size() && rc == 0; ++i) {
+        rc = eval_device(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps, s,
+                         cands[i]);
+        float ms = 0.0f;
+        if (rc == 0) rc = timed_run(cands[i], ms);
+        if (rc == 0) once.push_back({ms, i});
+    }
+    // second pass: the 12 fastest, median of 7
+    std::vector<Timed> med;
+    if (rc == 0) {
+        std::sort(once.begin(), once.end(), by_time);
+        for (size_t j = 0; j < once.size() && j < 12 && rc == 0; ++j) {
+            float ts[7];
+            for (int rep = 0; rep < 7 && rc == 0; ++rep) rc = timed_run(cands[once[j].second], ts[rep]);
+            if (rc) break;
+            std::sort(ts, ts + 7);
+            med.push_back({ts[3], once[j].second});
+        }
     }
     KernelChoice bestc = cands[0];
     if (rc == 0) {
-        // second pass: the candidates within 5 % of the best, 15 more runs each,
-        // interleaved so that slow drifts of the clock hit all of them alike
-        std::sort(med.begin(), med.end(),
-                  [](const std::pair<float, KernelChoice> &a, const std::pair<float, KernelChoice> &b) {
-                      return a.first < b.first;
-                  });
-        std::vector<KernelChoice> fin;
+        // third pass: the candidates within 5 % of the best median, 15 more
+        // runs each, interleaved so that slow drifts of the clock hit all of
+        // them alike
+        std::sort(med.begin(), med.end(), by_time);
+        std::vector<size_t> fin;
         for (const auto &m : med)
             if (m.first <= 1.05f * med[0].first && fin.size() < 4) fin.push_back(m.second);
+        std::sort(fin.begin(), fin.end());        // list order, for the tie-break
         std::vector<std::vector<float>> ts(fin.size());
         for (int rep = 0; rep < 15 && rc == 0 && fin.size() > 1; ++rep)
             for (size_t i = 0; i < fin.size() && rc == 0; ++i) {
                 float ms = 0.0f;
-                rc = timed_run(fin[i], ms);
+                rc = timed_run(cands[fin[i]], ms);
                 ts[i].push_back(ms);
             }
-        bestc = fin[0];
+        bestc = cands[med[0].second];
         if (rc == 0 && fin.size() > 1) {
+            std::vector<float> m(fin.size());
             float best = 1e30f;
             for (size_t i = 0; i < fin.size(); ++i) {
                 std::sort(ts[i].begin(), ts[i].end());
-                const float m = ts[i][ts[i].size() / 2];
-                if (m < best) { best = m; bestc = fin[i]; }
+                m[i] = ts[i][ts[i].size() / 2];
+                best = std::min(best, m[i]);
             }
+            for (size_t i = 0; i < fin.size(); ++i)
+                if (m[i] <= 1.01f * best) {
+                    bestc = cands[fin[i]];
+                    break;
+                }
         }
     }
     if (flush) cudaFree(flush);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    t->tuned[size_class(n_elec)] = bestc;
+    t->tuned[tune_key(n_elec, grads == nullptr)] = bestc;
     t->auto_mode = true;
     if (chosen) {
         chosen[0] = bestc.variant;
@@ -798,6 +852,12 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
         chosen[2] = bestc.warps;
         chosen[3] = bestc.sort;
     }
+    return BLIP_OK;
+}
+
+int blip_test_fail_alloc(int n)
+{
+    g_alloc_fail_after.store(n < 0 ? -1 : n);
     return BLIP_OK;
 }
 
@@ -918,7 +978,7 @@ int blip_graph_create(blip_table t, const double *pos, int n_elec, const int *wa
                          static_cast<float *>(values) + (size_t)e0 * L,
                          grads ? static_cast<float *>(grads) + (size_t)e0 * 3 * L : nullptr,
                          laps ? static_cast<float *>(laps) + (size_t)e0 * L : nullptr, s,
-                         pick(t, ne));
+                         pick(t, ne, grads == nullptr));
     }
     cudaError_t ee = cudaStreamEndCapture(s, &g->graph);
     if (e == cudaSuccess) e = ee;
@@ -1007,7 +1067,7 @@ extern "C" int blip_eval_sorted_noalloc(blip_table t, const double *pos, int n_e
     rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const KernelChoice kc = pick(t, n_elec);
+    const KernelChoice kc = pick(t, n_elec, grads == nullptr);
     if (t->n_k && !has_bloch_epilogue(kc)) return BLIP_ERR_INVALID_ARG;
     // the sort clears its histogram itself and overwrites everything else it
     // reads; no per-electron records (the kernels wrap the positions)

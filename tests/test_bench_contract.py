@@ -24,6 +24,11 @@ def test_reference_arm_json_line():
               "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    # the GPU arm prints the same metric and unit strings (one constant each)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["cpu_baseline"]["unit"] == bench.UNIT and d["e2e"]["unit"] == bench.UNIT
     assert d["value"] > 0 and d["higher_is_better"] is True
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["value"] == d["value"]

@@ -357,7 +357,7 @@ def test_tio2_all_at_once_and_one_at_a_time(pb):
         assert np.array_equal(a, b.cpu().numpy())
 
 
-@pytest.mark.parametrize("batch", [1, 32, 1536])
+@pytest.mark.parametrize("batch", [1, 32, 128, 1536])
 def test_tio2_batched_walkers(pb, batch):
     w, tab = cached_table("tio2")
     wb = bi.workload("tio2_batch", batch=batch)
@@ -379,10 +379,12 @@ def test_tio2_precision_storage_and_kinetic_energy(pb, storage):
     """Precision workload shape (1,536 electrons per walker, 768 orbitals):
     bound check on sampled electrons, and the Slater-only local kinetic
     energy of two walkers against the oracle, within the first-order bound
-    propagated from the elementwise output bounds.  The error per primitive
-    cell (64 cells) is reported beside the paper's 1e-3 hartree scale."""
+    propagated from the elementwise output bounds (its second-order terms are
+    products of the elementwise bounds, below 1e-6 of it here).  FP32 tables
+    must also meet the paper's ~1e-3 hartree per primitive cell (64 cells,
+    abstract and Sec. V.B); quantised tables are held to their propagated
+    bound only (they are for the Metropolis ratio, see the ratio tests)."""
     import json
-    import os
     from gpu_util import TAU32, U_Q, kinetic_error_bound, sum_abs_weights
     w, tab = cached_table("tio2")
     wp = bi.workload("tio2_precision", n_walkers=4)
@@ -413,11 +415,10 @@ def test_tio2_precision_storage_and_kinetic_energy(pb, storage):
         report["walkers"].append({"T_ref": T_ref, "T_gpu": T_gpu, "abs_err": err,
                                   "err_per_cell": err / 64.0, "bound": bound,
                                   "bound_per_cell": bound / 64.0, "cond": max(conds)})
-        assert err <= 1.05 * bound, (err, bound)
+        assert err <= bound, (err, bound)
+        if kind == pb.F32:
+            assert err / 64.0 <= 1e-3, err / 64.0
     print("\n" + json.dumps(report))
-    if os.path.isdir("gpurun_out"):
-        with open(f"gpurun_out/precision_{storage}.json", "w") as f:
-            json.dump(report, f, indent=1)
 
 
 @pytest.mark.parametrize("storage", ["c64", "bf16pair"])

@@ -123,3 +123,61 @@ def test_ratio_rejects_complex_tables_and_bad_args(pb):
         t.eval_ratio(pos, torch.zeros((3, 8), dtype=torch.float32, device="cuda"))
     L = pb.lib()
     assert L.blip_eval_ratio(None, None, 1, None, 0, None, None, None, 0, None) == -1
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_ratio_precision_tio2_shape(pb, storage):
+    """The acceptance ratio on the TiO2-shaped table (768 orbitals, two
+    walkers of 1,536 electrons, two spins of 768), the GPU use of the
+    paper's single-precision orbitals (Sec. V.B): every electron's trial
+    move r'_j = r_j + N(0, 0.3^2) is judged by xi_j = sum_l psi_l(r'_j)
+    (D_sigma^{-1})_{lj} (Eq. 11.12.23.1).  Checked against the FP64 ratio of
+    the oracle's orbitals under the propagated bound (coefficient rounding u
+    for quantised tables, FP32 rounding, the FP32 column), and every
+    Metropolis decision min(1, xi^2) > U (U seeded uniforms) that the GPU
+    ratio flips must lie inside that bound's band.  Prints the relative
+    error and the number of flipped decisions."""
+    import json
+    w = bi.workload("tio2")
+    tab = w.table()
+    base, offs = bi.walker_positions(w.lattice, 2, 1536, 1536, seed=103, move_sigma=0.0)
+    moved, _ = bi.walker_positions(w.lattice, 2, 1536, 1536, seed=103)
+    n = 768
+    cols = np.empty((len(moved), n), dtype=np.float32)
+    for wk in range(2):
+        v, _, _ = oracle.eval_stencil(w.grid, w.lattice, tab, base[1536 * wk:1536 * (wk + 1)])
+        for sp in range(2):
+            j0 = 1536 * wk + n * sp
+            Dinv = np.linalg.inv(v[n * sp:n * (sp + 1), :n])
+            cols[j0:j0 + n] = Dinv.T                   # electron j: column j of D^{-1}
+    kind = {"f32": pb.F32, "bf16": pb.BF16, "f16": pb.F16}[storage]
+    # the ratio contracts the first n orbitals: a table of exactly those
+    t = pb.BlipTable(w.grid, w.lattice, tab[..., :n], storage=kind)
+    ratio, _ = t.eval_ratio(torch.from_numpy(moved).cuda(), torch.from_numpy(cols).cuda(),
+                            torch.from_numpy(offs).cuda(), sort=1)
+    torch.cuda.synchronize()
+    xi = ratio.cpu().numpy().astype(np.float64)[:, 0]
+    rv, _, _, mag = oracle.eval_stencil(w.grid, w.lattice, tab[..., :n], moved, absmag=True)
+    c64 = cols.astype(np.float64)
+    ref = (rv * c64).sum(1)
+    tau = TAU32 + {"f32": 0.0, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}[storage]
+    bound = (np.abs(c64) * tau * mag[:, 0]).sum(1) \
+        + 2 * (n / 32 + 8) * 2.0 ** -24 * np.abs(rv * c64).sum(1)
+    if kind == pb.F16:                                 # FP16 subnormal floor
+        s_l = np.abs(tab[..., :n]).reshape(-1, n).max(0)
+        bound += 2.0 ** -25 * (np.abs(c64) * s_l[None, :]).sum(1)
+    err = np.abs(xi - ref)
+    assert (err <= bound).all(), float(np.max(err / bound))
+    U = bi.uniform(bi.stream_key(103, 0xACC), np.arange(len(moved), dtype=np.uint64))
+    acc_ref = np.minimum(1.0, ref ** 2) > U
+    acc_gpu = np.minimum(1.0, xi ** 2) > U
+    flips = acc_ref != acc_gpu
+    band = np.abs(np.minimum(1.0, ref ** 2) - U) <= 2 * np.abs(ref) * bound + bound ** 2
+    assert (band[flips]).all()
+    rel = err / np.abs(ref)
+    print("\n" + json.dumps({"storage": storage, "max_rel_err": float(rel.max()),
+                             "rms_rel_err": float(np.sqrt(np.mean(rel ** 2))),
+                             "median_rel_err": float(np.median(rel)),
+                             "flipped_decisions": int(flips.sum()), "moves": len(moved),
+                             "accepted_ref": int(acc_ref.sum())}))
+    assert t.status() == 0

@@ -116,3 +116,36 @@ def test_noalloc_with_the_staged_tile_kernel(pb):
             assert torch.equal(torch.nan_to_num(r, nan=7.0), torch.nan_to_num(o, nan=7.0)), cfg
         assert bool(torch.isnan(out[0][17]).all())
         assert t.status() & pb.STATUS_NONFINITE_POS
+
+
+@pytest.mark.parametrize("cfg", [(11, 1, 8, 1), (11, 1, 8, 2), (10, 1, 4, 1), (5, 2, 4, 1),
+                                 (5, 4, 8, 1), (2, 2, 8, 1), (9, 1, 8, 2), (3, 2, 4, 2),
+                                 (6, 1, 8, 1), (7, 1, 8, 1)])
+def test_noalloc_with_each_sorted_kernel(pb, cfg):
+    """Every kernel the entry point can run on the sorted order - without the
+    per-electron geometry records blip_eval's sort makes, so each kernel
+    wraps the positions itself - against blip_eval with the same kernel
+    choice, on two calls in a row, within the parity tolerance."""
+    grid = (20, 18, 16)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, 300, seed=25)
+    t = pb.BlipTable(grid, lat, tab, storage=pb.F32)
+    t.set_kernel(*cfg)
+    for seed, n in ((26, 3000), (27, 1777)):
+        pos = bi.uniform_positions(lat, n, seed=seed) + 2.0 * lat[2]
+        dpos = torch.from_numpy(pos).cuda()
+        ref = t.eval(dpos)
+        out = t.alloc_outputs(n)
+        for o in out:
+            o.fill_(float("nan"))
+        rc = _noalloc(pb, t, dpos, None, out)
+        assert rc == 0, pb.lib().blip_strerror(rc)
+        torch.cuda.synchronize()
+        idx = np.arange(0, n, 7)
+        _, _, _, mag = oracle.eval_stencil(grid, lat, tab, pos[idx], absmag=True)
+        bounds = [TAU32 * mag[:, 0], TAU32 * mag[:, 1:4], TAU32 * mag[:, 4]]
+        for r, o, b in zip(ref, out, bounds):
+            diff = np.abs(o[idx].cpu().numpy().astype(np.float64) - r[idx].cpu().numpy())
+            assert (diff <= b + 1e-30).all(), cfg
+            assert not torch.isnan(o).any(), cfg
+    assert t.status() == 0
