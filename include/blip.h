@@ -60,6 +60,8 @@ extern "C" {
 #define BLIP_STATUS_FAR_POS        0x2 /* |fractional coordinate| > 2^40: precision lost */
 #define BLIP_STATUS_BAD_OFFSETS    0x4 /* walker offsets not monotone or out of range    */
 #define BLIP_STATUS_TIMEOUT        0x8 /* a bounded wait in a kernel gave up             */
+#define BLIP_STATUS_LAYOUT         0x10 /* a kernel's shared memory lacked the alignment its
+                                           operand layout needs: it wrote no outputs       */
 
 /* ---- storage kinds ---------------------------------------------------- */
 typedef enum {
@@ -226,21 +228,34 @@ int blip_info(blip_table t, long long out[8]);
  *                 chunk) items; each warp prefetches the next electron's
  *                 position (cp.async) and runs its FP64 wrap while the
  *                 current rows are in flight (FP32 tables, one chunk per
- *                 warp; not with k-points)
+ *                 warp; not with k-points);
+ *             12: tensor cores for dense batches (always sorts): parts of up
+ *                 to 25 electrons from at most 5 consecutive cells along a_3
+ *                 of one grid column share the union of their stencils,
+ *                 16 columns x 8 rows; the contraction over it is a matrix
+ *                 product on the tensor cores (tcgen05, accumulators in
+ *                 tensor memory), the coefficients as stored (16-bit tables)
+ *                 or, for FP32 tables, as two FP16 planes of a / s_l with
+ *                 s_l a power of two (22 significant bits, made on first
+ *                 use), times the weights split into two 16-bit parts;
+ *                 agrees with the other variants to rounding, not bitwise;
+ *                 not with k-points
  *   chunks     variants 1, 3, 4, 6, 7: orbital chunks (32 lanes x 16 bytes) per
  *              warp, 1..3 (1 for 16-bit storage); variants 9, 11: 1; variant 2: consumer warps
  *              per CTA, 1..8; variant 5: electrons per group, 2 or 4;
- *              variant 8: tile cells along a_3, 2 or 4; variant 10: 1
+ *              variant 8: tile cells along a_3, 2 or 4; variants 10, 12: 1
  *   warps      variants 1, 3, 4, 6, 7, 9, 11: warps per block, 1..16; variant 2:
  *              shared-memory pipeline stages, 2..32; variant 5: warps per
  *              block, 1..8; variant 8: consumer warps per CTA, 12 or 16;
- *              variant 10: 4
+ *              variant 10: 4; variant 12: 1
  *   sort       0: electrons in input order; 1: sort by grid cell first (L2
  *              reuse for large batches); 2 (variants 1, 3, 4, 9, 11): sorted, and
  *              the warps' work ordered by orbital chunk group first, so the
  *              warps in flight cover more electrons with a smaller slice of
  *              each row
- * Errors: INVALID_ARG for values outside those sets.
+ * Errors: INVALID_ARG for values outside those sets; variant 12 may also
+ * return OOM or CUDA (its column list and, for FP32 tables, its two FP16
+ * planes are made here).
  */
 int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort);
 
@@ -278,8 +293,9 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
  *            koffs[n_k] = n_orb
  * The phase uses the unwrapped fractional coordinates, reduced mod 1 in
  * FP64.  Errors: INVALID_ARG, UNSUPPORTED_DTYPE (real tables).  The bulk-copy,
- * staged-tile, split-stencil and persistent kernels (variants 2, 8, 10 and
- * 11) have no Bloch epilogue and are not used while k-points are set.
+ * staged-tile, split-stencil, persistent and tensor-core kernels (variants
+ * 2, 8, 10, 11 and 12) have no Bloch epilogue and are not used while
+ * k-points are set.
  */
 int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koffs);
 

@@ -17,11 +17,12 @@ from . import _build
 
 __all__ = ["lib", "BlipTable", "BlipError", "sm_update", "F32", "BF16", "F16", "C64", "BF16PAIR",
            "NORM_BSPLINE", "NORM_ALFE_GILLAN", "STATUS_NONFINITE_POS", "STATUS_FAR_POS",
-           "STATUS_BAD_OFFSETS", "STATUS_TIMEOUT", "EXPORTED"]
+           "STATUS_BAD_OFFSETS", "STATUS_TIMEOUT", "STATUS_LAYOUT", "EXPORTED"]
 
 F32, BF16, F16, C64, BF16PAIR = 0, 1, 2, 3, 4
 NORM_BSPLINE, NORM_ALFE_GILLAN = 0, 1
 STATUS_NONFINITE_POS, STATUS_FAR_POS, STATUS_BAD_OFFSETS, STATUS_TIMEOUT = 1, 2, 4, 8
+STATUS_LAYOUT = 16
 ERRORS = {0: "ok", -1: "invalid argument", -2: "singular lattice", -3: "out of memory",
           -4: "CUDA error", -5: "unsupported storage kind", -6: "no sm_103 CUDA device",
           -7: "batch too large for the fixed no-allocation scratch"}

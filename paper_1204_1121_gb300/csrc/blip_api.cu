@@ -59,6 +59,14 @@ struct blip_table_s {
     // tensor maps of the table for the staged-tile kernel (tile depth 2, 4)
     TmaDesc tmap[2] = {};
     bool tmap_ok[2] = {false, false};
+    // tensor-core kernel: grid-column keys in sort order, BF16 planes of an
+    // FP32 table, the tensor map of its operand (made on first use)
+    int *d_cols = nullptr;
+    int ncols = 0;
+    void *d_planes = nullptr;
+    float *d_tc_scales = nullptr;
+    TmaDesc tc_tmap = {};
+    bool tc_ready = false;
     // Bloch k-points (complex tables)
     int n_k = 0;
     int koff[kMaxKpoints + 1] = {};
@@ -250,11 +258,54 @@ int staged_tmap(blip_table_s *t, int tz, const TmaDesc **out)
     return BLIP_OK;
 }
 
-// The bulk-copy, staged-tile and split-stencil kernels have no Bloch epilogue.
+// The bulk-copy, staged-tile, split-stencil, persistent and tensor-core
+// kernels have no Bloch epilogue.
 bool has_bloch_epilogue(const KernelChoice &kc)
 {
     return kc.variant != VAR_BULK && kc.variant != VAR_STAGED && kc.variant != VAR_SPLIT &&
-           kc.variant != VAR_REGISTER_PERSIST;
+           kc.variant != VAR_REGISTER_PERSIST && kc.variant != VAR_TENSOR;
+}
+
+// What the tensor-core kernel needs beyond the table, made once (outside
+// stream capture): the keys of the grid columns' first cells in sort order,
+// for FP32 tables their two scaled FP16 planes, and the operand tensor map.
+int tc_prepare(blip_table_s *t)
+{
+    if (t->tc_ready) return BLIP_OK;
+    std::vector<int> keys;
+    keys.reserve((size_t)t->grid[0] * t->grid[1]);
+    for (int x = 0; x < t->grid[0]; ++x)
+        for (int y = 0; y < t->grid[1]; ++y) keys.push_back(sort_cell_key(t->geo, x, y, 0));
+    std::sort(keys.begin(), keys.end());
+    if (!t->d_cols) {
+        CK(dev_alloc(&t->d_cols, sizeof(int) * keys.size()));
+        CK(cudaMemcpy(t->d_cols, keys.data(), sizeof(int) * keys.size(), cudaMemcpyHostToDevice));
+        t->ncols = (int)keys.size();
+    }
+    const void *operand = t->d_table;
+    long long rows_total = t->rows;
+    if (t->elem == ELEM_F32) {
+        if (2 * t->rows >= (1LL << 31)) return BLIP_ERR_INVALID_ARG;
+        if (!t->d_planes) {
+            const long long n = t->rows * t->row_stride;
+            unsigned int *bits = nullptr;
+            CK(dev_alloc(&t->d_tc_scales, sizeof(float) * (size_t)t->row_stride));
+            CK(dev_alloc(&t->d_planes, (size_t)n * 2 * 2));
+            CK(dev_alloc(&bits, sizeof(unsigned int) * (size_t)t->row_stride));
+            cudaError_t e = launch_split_pairs(static_cast<const float *>(t->d_table), t->rows,
+                                               t->row_stride, t->Lreal, bits, t->d_tc_scales,
+                                               t->d_planes, t->own_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(t->own_stream);
+            cudaFree(bits);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
+        operand = t->d_planes;
+        rows_total = 2 * t->rows;
+    }
+    CK(make_tc_tmap(operand, t->elem == ELEM_F32 ? ELEM_F16 : t->elem, t->row_stride, rows_total,
+                    &t->tc_tmap));
+    t->tc_ready = true;
+    return BLIP_OK;
 }
 
 // Launch parameters of an evaluation with kernel choice kc; the evaluation
@@ -314,6 +365,14 @@ int launch_choice(blip_table_s *t, const EvalParams &p, const KernelChoice &kc, 
         if (rc) return rc;
         CK(launch_staged(p, t->elem, kc.chunks, kc.warps, cell_end, *tm, t->sm_count, t->test_stall,
                          stream));
+    } else if (kc.variant == VAR_TENSOR) {
+        if (!t->tc_ready) return BLIP_ERR_INVALID_ARG;   // prepared by blip_set_kernel / autotune
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, p.n_elec, scratch, &keys, &cell_end);
+        EvalParams pt = p;
+        if (t->elem == ELEM_F32) pt.scales = t->d_tc_scales;   // the planes' power-of-two scales
+        CK(launch_tc(pt, t->elem, cell_end, t->d_cols, t->ncols, t->rows, t->tc_tmap, t->sm_count,
+                     t->test_stall, stream));
     } else if (kc.variant == VAR_SPLIT) {
         CK(launch_split(p, t->elem, stream));
     } else if (kc.variant == VAR_REGISTER_PERSIST) {
@@ -333,7 +392,8 @@ int eval_device(blip_table_s *t, const double *pos, int n_elec, const int *offs,
     if (n_elec == 0) return BLIP_OK;
     if (t->n_k && !has_bloch_epilogue(kc)) return BLIP_ERR_INVALID_ARG;
     EvalParams p = make_params(t, pos, n_elec, offs, n_walkers, values, grads, laps, kc);
-    if (kc.sort || kc.variant == VAR_GROUPED || kc.variant == VAR_STAGED) {
+    if (kc.sort || kc.variant == VAR_GROUPED || kc.variant == VAR_STAGED ||
+        kc.variant == VAR_TENSOR) {
         int *perm = nullptr;
         const ElecGeo *rec = nullptr;
         const bool want_rec = t->n_k == 0 && kc.variant != VAR_BULK;
@@ -360,7 +420,7 @@ void free_table(blip_table_s *t)
 {
     if (!t) return;
     if (!t->d_table && !t->d_scales && !t->d_status && !t->stage && !t->scratch &&
-        !t->own_stream) {
+        !t->own_stream && !t->d_cols && !t->d_planes && !t->d_tc_scales) {
         delete t;
         return;
     }
@@ -372,6 +432,9 @@ void free_table(blip_table_s *t)
     if (t->d_status) cudaFree(t->d_status);
     if (t->stage) cudaFree(t->stage);
     if (t->scratch) cudaFree(t->scratch);
+    if (t->d_cols) cudaFree(t->d_cols);
+    if (t->d_planes) cudaFree(t->d_planes);
+    if (t->d_tc_scales) cudaFree(t->d_tc_scales);
     if (t->own_stream) cudaStreamDestroy(t->own_stream);
     if (cur >= 0 && cur != t->device) cudaSetDevice(cur);
     delete t;
@@ -683,6 +746,12 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort)
         if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
         if ((chunks != 2 && chunks != 4) || (warps != 12 && warps != 16)) return BLIP_ERR_INVALID_ARG;
         sort = 1;
+    } else if (variant == VAR_TENSOR) {
+        // one configuration; always evaluated in cell order; no Bloch epilogue
+        if (t->n_k || chunks != 1 || warps != 1) return BLIP_ERR_INVALID_ARG;
+        sort = 1;
+        const int rc = tc_prepare(t);
+        if (rc) return rc;
     } else if (variant == VAR_BULK) {
         if (t->n_k) return BLIP_ERR_INVALID_ARG;          // no Bloch epilogue in this kernel
         // chunks = consumer warps per CTA (chunks per tile), warps = pipeline stages
@@ -752,6 +821,10 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
         if (srt && !t->n_k)
             for (int tz : {2, 4})
                 for (int cw : {12, 16}) cands.push_back(KernelChoice{VAR_STAGED, tz, cw, 1});
+        // tensor cores once the batch holds half an electron per cell or more
+        const long long cells = (long long)t->grid[0] * t->grid[1] * t->grid[2];
+        if (srt && !t->n_k && 2LL * n_elec >= cells && tc_prepare(t) == BLIP_OK)
+            cands.push_back(KernelChoice{VAR_TENSOR, 1, 1, 1});
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

@@ -26,8 +26,10 @@ enum Variant {
     VAR_REGISTER_PIPE3 = 9,   // as 3 with two batches in flight (FP32, 1 chunk per warp)
     VAR_SPLIT = 10,           // 4 warps per (electron, chunk), one a_1 slab of the
                               // stencil each: one round of latency (small launches)
-    VAR_REGISTER_PERSIST = 11 // as 9 with resident warps that walk the items and
+    VAR_REGISTER_PERSIST = 11,// as 9 with resident warps that walk the items and
                               // prefetch the next electron's geometry (no k-points)
+    VAR_TENSOR = 12           // parts of up to 25 electrons of <= 5 cells of one grid
+                              // column: tensor-core products over their union rows
 };
 
 constexpr int kMaxKpoints = 16;
@@ -177,6 +179,25 @@ cudaError_t make_staged_tmap(const void *table, int elem, long long row_stride, 
 // and tz.  stall != 0 is the same test hook as for launch_bulk.
 cudaError_t launch_staged(const EvalParams &p, int elem, int tz, int cw, const int *cell_end,
                           const TmaDesc &tmap, int sm_count, int stall, cudaStream_t stream);
+
+// Tensor map of the operand planes of the tensor-core kernel: a 2-D tensor
+// [rows_total][row_stride] of 16-bit elements (elem BF16 or F16), box 64
+// elements x 8 rows, 128-byte swizzle.
+cudaError_t make_tc_tmap(const void *base, int elem, long long row_stride, long long rows_total,
+                         TmaDesc *out);
+// The two FP16 planes of an FP32 table for the tensor-core kernel: scales[l]
+// = the smallest power of two >= max |a_l| (1 for zero components), planes
+// [2][rows][row_stride] = RN(a / s_l) and RN(a / s_l - hi).  bits: scratch of
+// row_stride words.
+cudaError_t launch_split_pairs(const float *src, long long rows, long long row_stride, int Lreal,
+                              unsigned int *bits, float *scales, void *dst, cudaStream_t stream);
+// Launch the tensor-core kernel (needs the sort): elem = ELEM_BF16 / ELEM_F16
+// (tmap over the table, p.scales its per-component scales or null) or ELEM_F32
+// (tmap over its two FP16 planes, each plane_rows rows, p.scales their
+// power-of-two scales); cols: the ncols column keys in sort order.
+cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
+                      int ncols, long long plane_rows, const TmaDesc &tmap, int sm_count, int stall,
+                      cudaStream_t stream);
 
 // Launch the split-stencil kernel: a block of 4 warps per (electron, chunk),
 // warp q contracting the 16 sites of a_1 slab q, partial sums added in a

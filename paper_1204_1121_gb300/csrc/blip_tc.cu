@@ -1,0 +1,843 @@
+// Tensor-core evaluation kernel for dense sorted batches (variant 12).
+//
+// When a quasi-simultaneous batch (Sec. IV.A) holds many electrons per grid
+// cell, the electrons of a few neighbouring cells share their stencil rows
+// (Eq. 7), and the contraction of Eq. 11.12.24.1 over those rows becomes a
+// dense matrix product.  A part is up to kNE electrons from at most 5
+// consecutive cells along a_3 of one grid column (x, y); every stencil of
+// the part lies in the union of 16 stencil columns (x - 1 .. x + 2,
+// y - 1 .. y + 2) x 8 stored rows (z0 .. z0 + 7, the ghost-plane layout).
+// With K = 128 union rows:
+//
+//     D^T[l][(j, o)] = sum_k  a[k][l]  W_o^{(j)}[k]
+//
+// M = 128 orbital components per tile (the stored rows, orbital-contiguous,
+// are the MN-major A operand as they stand), N = 5 x electrons (value,
+// d/dx, d/dy, d/dz, Laplacian weights of each electron, zero outside its 64
+// sites; the K-major B operand, built on the chip).  The weights are split
+// into two 16-bit parts (hi + lo, the same type as the table) so the
+// weight rounding is about 2^-17 relative; the coefficients enter as stored.
+// FP32 tables enter as two FP16 planes of a / s_l (s_l a power of two at or
+// above the component's largest |a|, so the division is exact): hi = RN(a /
+// s_l), lo = RN(a / s_l - hi), 22 significant bits; with FP16 weights split
+// the same way, three products per K step (hi.hi, hi.lo, lo.hi) leave out
+// lo.lo, below 2^-22 relative; s_l is applied in the epilogue.  Products are
+// accumulated in FP32 in tensor memory.
+//
+// Persistent grid, one CTA per SM, 14 warps:
+//   warp 0      TMA producer: per (part, M tile) the 16 columns x 2 orbital
+//               halves of 8 rows x 64 components (one 128-byte-swizzled
+//               1 KB box each, per plane) into a 3-stage ring;
+//   warp 1      allocates tensor memory and issues the MMAs (one thread):
+//               per M tile, 8 K steps x planes products into one of two
+//               128-column FP32 accumulators, then tcgen05.commit to the
+//               stage's empty barrier and the accumulator's full barrier;
+//   warps 2-9   epilogue, two warps per lane quarter of the accumulator:
+//               tensor memory -> registers (tcgen05.ld), scale, streaming
+//               stores through a per-column output-row pointer (a warp
+//               writes 32 consecutive components of one output);
+//   warps 10-13 weights: the part's electrons (geometry from the sort's
+//               per-slot records, or the FP64 wrap), their 64 x 5 weights
+//               split into 16-bit planes, written as B operand core
+//               matrices into one of two buffers.
+// Every wait is bounded (about 2 s of global time): a wait that runs out
+// sets BLIP_STATUS_TIMEOUT and an abort flag; every role then winds down,
+// the producer waits (bounded) for its copies in flight and the MMA thread
+// for its products before the tensor memory is freed.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "blip_mbar.cuh"
+
+namespace blip {
+
+namespace {
+
+using namespace dev;
+using namespace mb;
+
+constexpr int kNE = 25;                 // electrons per part: N = 5 kNE <= 128
+constexpr int kSegCells = 5;            // cells along a_3 per part
+constexpr int kWin = 8;                 // stored rows per stencil column of a part
+constexpr int kCols = 16;               // stencil columns (4 x 4)
+constexpr int kK = kCols * kWin;        // 128 union rows = K
+constexpr int kMT = 128;                // orbital components per M tile
+constexpr int kNmax = 128;
+constexpr int kEpiWarps = 8;           // two per tensor-memory lane quarter
+constexpr int kThreads = 32 * (2 + kEpiWarps + 4);
+constexpr uint32_t kBox = 1024;                          // 8 rows x 128 bytes
+constexpr uint32_t kStage = kMT * kK * 2;                // one operand plane of one M tile: 32 KB
+constexpr uint32_t kPlaneW = kNmax * kK * 2;             // one weight plane: 32 KB
+constexpr uint32_t kTmemCols = 256;                      // two 128-column accumulators
+
+// Shapes of one instantiation: APL coefficient planes per M tile (1: the
+// 16-bit table as stored; 2: an FP32 table as two FP16 planes, hi + lo, of
+// the coefficient over a power-of-two per-component scale), two 16-bit weight
+// planes (hi + lo) in two buffers (the next part's weights are built while
+// the current part's products run), a ring of 3 operand stages.
+template <int APL> struct TcCfg {
+    static constexpr int WPL = 2;
+    static constexpr int WB = 2;
+    static constexpr int STAGES = 3;
+    static constexpr uint32_t W_BUF = WPL * kPlaneW;
+};
+
+// Part bookkeeping shared by the weight warps (writers), the MMA thread and
+// the epilogue (readers), one per weight buffer.
+struct __align__(16) PartInfo {
+    int cnt;            // electrons, or -1 for "no more parts"
+    int n;              // MMA N: outputs x cnt rounded up to 16
+    int pad[2];
+    float *dst[kNmax];  // output row of accumulator column NO j + o (electron j, output o)
+};
+
+struct TcArgs {
+    const int *cell_end;   // sort: one past the last slot of each key
+    const int *cols;       // column keys (key of cell (x, y, 0)) in sort order
+    int ncols;
+    int P;                 // key of positions without a cell
+    int mt;                // M tiles (ceil(Lreal / 128))
+    int plane_rows;        // rows of one coefficient plane in the tensor map
+    int stall;             // test hook: the MMA thread never releases the first stage
+};
+
+template <int APL>
+constexpr size_t tc_smem()
+{
+    return TcCfg<APL>::STAGES * kStage +
+           TcCfg<APL>::WB * TcCfg<APL>::W_BUF + 2 * sizeof(PartInfo) + 256;
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMA helpers (inline PTX)
+// ---------------------------------------------------------------------------
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (16-byte units), the sm_100 descriptor version, swizzle mode.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t swizzle)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) |
+           ((uint64_t)(swizzle & 7u) << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B of one
+// 16-bit type (fmt 0 = FP16, 1 = BF16), A MN-major, B K-major, M = 128, N.
+__device__ __forceinline__ uint32_t instr_desc(int n, int fmt)
+{
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | (1u << 15) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kMT >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id,
+                                        uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Bounded wait that also gives up once another warp has aborted.
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, unsigned parity, volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 31u) == 0 && (*abort_flag || global_ns() - t0 > WAIT_LIMIT_NS)) return false;
+    }
+}
+
+__device__ __forceinline__ void raise_abort(const EvalParams &p, volatile int *abort_flag)
+{
+    *abort_flag = 1;
+    atomicOr(p.status, BLIP_STATUS_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// parts: the same deterministic walk for the producer and the weight warps
+// ---------------------------------------------------------------------------
+
+struct Cursor {
+    int z;        // current cell along a_3
+    int used;     // electrons of cell z already in earlier parts
+    int sbase;    // first slot of cell z
+};
+
+__device__ __forceinline__ void cursor_init(const TcArgs &a, int k0, Cursor &c)
+{
+    c.z = 0;
+    c.used = 0;
+    c.sbase = k0 ? a.cell_end[k0 - 1] : 0;
+}
+
+// Next part of the column whose cell (x, y, 0) has key k0: up to kNE
+// electrons from at most kSegCells consecutive cells, starting at the first
+// cell with electrons left; a cell with more than kNE electrons gives parts
+// of kNE of its own.  Returns false when the column is done.
+__device__ __forceinline__ bool next_part(const TcArgs &a, int k0, int n3, Cursor &c, int &z0,
+                                          int &s0, int &cnt)
+{
+    for (;;) {
+        if (c.z >= n3) return false;
+        const int end = a.cell_end[k0 + c.z];
+        if (end - c.sbase - c.used > 0) break;
+        c.sbase = end;
+        c.used = 0;
+        ++c.z;
+    }
+    z0 = c.z;
+    s0 = c.sbase + c.used;
+    const int end0 = a.cell_end[k0 + c.z];
+    if (end0 - s0 >= kNE) {
+        cnt = kNE;
+        c.used += kNE;
+        return true;
+    }
+    cnt = end0 - s0;
+    c.sbase = end0;
+    c.used = 0;
+    ++c.z;
+    while (c.z < n3 && c.z < z0 + kSegCells) {
+        const int e = a.cell_end[k0 + c.z];
+        if (cnt + (e - c.sbase) > kNE) break;
+        cnt += e - c.sbase;
+        c.sbase = e;
+        ++c.z;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void column_xy(const Geometry &g, int k0, int &x, int &y)
+{
+    // invert sort_cell_key(x, y, 0) = ((sb * 16 + br) * 64 + col) * n3
+    const int q = k0 / g.n[2];
+    const int col = q & 63, br = (q >> 6) & 15, sb = q >> 10;
+    const int nsy = (g.n[1] + 31) >> 5;
+    x = (sb / nsy) * 32 + (br >> 2) * 8 + (col >> 3);
+    y = (sb % nsy) * 32 + (br & 3) * 8 + (col & 7);
+}
+
+// Bit pattern of a 16-bit value of type T.
+template <typename T> __device__ __forceinline__ unsigned short to_bits(float v);
+template <> __device__ __forceinline__ unsigned short to_bits<__nv_bfloat16>(float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <> __device__ __forceinline__ unsigned short to_bits<__half>(float v)
+{
+    return __half_as_ushort(__float2half_rn(v));
+}
+template <typename T> __device__ __forceinline__ float from_bits(unsigned short b);
+template <> __device__ __forceinline__ float from_bits<__nv_bfloat16>(unsigned short b)
+{
+    return __bfloat162float(__ushort_as_bfloat16(b));
+}
+template <> __device__ __forceinline__ float from_bits<__half>(unsigned short b)
+{
+    return __half2float(__ushort_as_half(b));
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+
+// T: the 16-bit operand type; APL: coefficient planes (1: the 16-bit table;
+// 2: an FP32 table as two scaled FP16 planes).
+template <typename T, int APL, bool VONLY>
+__global__ void __launch_bounds__(kThreads, 1)
+    blip_eval_tc(EvalParams p, TcArgs a, const __grid_constant__ CUtensorMap tmap)
+{
+    using Cfg = TcCfg<APL>;
+    constexpr int WPL = Cfg::WPL, WB = Cfg::WB, NS = Cfg::STAGES;
+    constexpr int NO = VONLY ? 1 : 5;                    // outputs per electron
+    constexpr int FMT = std::is_same<T, __nv_bfloat16>::value ? 1 : 0;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    // the 128-byte-swizzled operand stages need 1024-byte alignment: give up
+    // (status bit, no output) if the dynamic shared memory does not have it
+    if (smem_addr(smem) & 1023u) {
+        if (threadIdx.x == 0) atomicOr(p.status, BLIP_STATUS_LAYOUT);
+        return;
+    }
+    unsigned char *stageA = smem;
+    unsigned char *wbuf = smem + NS * kStage;
+    PartInfo *info = reinterpret_cast<PartInfo *>(wbuf + WB * Cfg::W_BUF);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(info + 2);
+    uint64_t *a_full = bars, *a_empty = bars + NS;
+    uint64_t *w_full = bars + 2 * NS, *w_empty = w_full + 2, *epi_done = w_full + 4;
+    uint64_t *acc_full = w_full + 6, *acc_empty = w_full + 8, *drain = w_full + 10;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n2 = p.geo.n[1], n3 = p.geo.n[2];
+    check_offsets(p);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(a_full + s, 1);
+            mbar_init(a_empty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(w_full + b, 1);
+            mbar_init(w_empty + b, 1);
+            mbar_init(epi_done + b, kEpiWarps);
+            mbar_init(acc_full + b, 1);
+            mbar_init(acc_empty + b, kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        long long fill = 0;
+        bool ok = true;
+        // this lane's box: stencil column c = lane / 2, orbital half lane % 2
+        const int c = lane >> 1, h = lane & 1;
+        for (int ci = blockIdx.x; ci < a.ncols && ok; ci += gridDim.x) {
+            const int k0 = a.cols[ci];
+            int x, y;
+            column_xy(p.geo, k0, x, y);
+            int gx = x - 1 + (c >> 2), gy = y - 1 + (c & 3);
+            gx += gx < 0 ? p.geo.n[0] : 0;
+            gx -= gx >= p.geo.n[0] ? p.geo.n[0] : 0;
+            gy += gy < 0 ? n2 : 0;
+            gy -= gy >= n2 ? n2 : 0;
+            const int colrow = (gx * n2 + gy) * (n3 + 3);
+            Cursor cur;
+            cursor_init(a, k0, cur);
+            int z0, s0, cnt;
+            while (ok && next_part(a, k0, n3, cur, z0, s0, cnt)) {
+                for (int m = 0; m < a.mt && ok; ++m)
+                    for (int pl = APL - 1; pl >= 0; --pl) {      // FP32: lo, mid, hi
+                        const int s = (int)(fill % NS);
+                        const long long k = fill / NS;
+                        if (k > 0) {
+                            const bool got = wait_bar(a_empty + s, (unsigned)((k - 1) & 1), abort_flag);
+                            if (!__all_sync(FULL, got)) {
+                                if (lane == 0) raise_abort(p, abort_flag);
+                                ok = false;
+                                break;
+                            }
+                        }
+                        if (lane == 0) mbar_expect_tx(a_full + s, kStage);
+                        __syncwarp();
+                        tma_load_2d(stageA + s * kStage + c * kBox + h * (kStage / 2), &tmap,
+                                    m * kMT + 64 * h, pl * a.plane_rows + colrow + z0, a_full + s);
+                        ++fill;
+                    }
+            }
+        }
+        // drain: the copies of the last fills must land before the CTA exits
+        for (long long f = fill > NS ? fill - NS : 0; f < fill; ++f) {
+            const bool got = mbar_wait(a_full + (int)(f % NS), (unsigned)((f / NS) & 1));
+            if (!__all_sync(FULL, got) && lane == 0) atomicOr(p.status, BLIP_STATUS_TIMEOUT);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issue (one thread) ----------------
+        long long fill = 0, tile = 0;
+        bool ok = true;
+        const uint32_t stage_base = smem_addr(stageA), w_base = smem_addr(wbuf);
+        for (long long part = 0; ok; ++part) {
+            const int wi = (int)(part & 1);                  // info slot
+            const int wb = WB == 2 ? wi : 0;                 // weight buffer
+            if (!wait_bar(w_full + wi, (unsigned)((part >> 1) & 1), abort_flag)) {
+                if (lane == 0) raise_abort(p, abort_flag);
+                break;
+            }
+            if (info[wi].cnt < 0) break;
+            const uint32_t id = instr_desc(info[wi].n, FMT);
+            const uint32_t sw = w_base + wb * Cfg::W_BUF;
+            for (int m = 0; m < a.mt && ok; ++m) {
+                const int ab = (int)(tile & 1);
+                if (tile >= 2) {
+                    const bool got = wait_bar(acc_empty + ab, (unsigned)(((tile >> 1) - 1) & 1), abort_flag);
+                    if (!__all_sync(FULL, got)) {
+                        if (lane == 0) raise_abort(p, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                }
+                const uint32_t d = tmem + (uint32_t)(ab * kNmax);
+                for (int pl = APL - 1; pl >= 0; --pl) {
+                    const int s = (int)(fill % NS);
+                    const bool got = wait_bar(a_full + s, (unsigned)((fill / NS) & 1), abort_flag);
+                    if (!__all_sync(FULL, got)) {
+                        if (lane == 0) raise_abort(p, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (lane == 0) {
+                        const uint32_t sa = stage_base + s * kStage;
+                        // a 16-bit table (pl = 0) meets both weight planes; of
+                        // an FP32 table's planes the lo one meets the hi weights
+                        // only (lo x lo is below 2^-22 relative)
+                        const int nw = APL == 1 ? WPL : 2 - pl;
+#pragma unroll 1
+                        for (int ks = 0; ks < kK / 16; ++ks) {
+                            // A: 2 stencil columns (16 rows) per K step, 1 KB per
+                            // column, the second 64-component half kStage/2 on;
+                            // B: K groups of 8 at 2 KB, N groups of 8 rows at 128 B
+                            const uint64_t ad = smem_desc(sa + ks * 2 * kBox, kStage / 2, kBox, 2);
+                            for (int pw = 0; pw < nw; ++pw) {
+                                const uint64_t bd = smem_desc(sw + pw * kPlaneW + ks * 2 * 2048u,
+                                                              2048u, 128u, 0);
+                                const bool first = pl == APL - 1 && ks == 0 && pw == 0;
+                                mma_f16(d, ad, bd, id, first ? 0u : 1u);
+                            }
+                        }
+                        if (!(a.stall && fill == 0)) mma_commit(a_empty + s);
+                        if (pl == 0) {
+                            mma_commit(acc_full + ab);
+                            if (m == a.mt - 1) mma_commit(w_empty + wi);
+                        }
+                    }
+                    __syncwarp();
+                    ++fill;
+                }
+                if (ok) ++tile;
+            }
+        }
+        // every product issued (also those of a tile cut short by an abort)
+        // must be done before the tensor memory is freed
+        if (lane == 0) {
+            mma_commit(drain);
+            if (!mbar_wait(drain, 0)) atomicOr(p.status, BLIP_STATUS_TIMEOUT);
+        }
+        __syncwarp();
+    } else if (warp < 2 + kEpiWarps) {
+        // ---------------- epilogue ----------------
+        // warps 2 .. 9: lane quarter q = warp % 4 of the accumulator; the two
+        // warps of a quarter take alternate 32-column chunks
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int et = threadIdx.x - 64;             // 0 .. 32 kEpiWarps - 1
+        const size_t L = (size_t)p.Lreal;
+        // positions without a cell (last sort bucket): NaN outputs
+        {
+            const int nan0 = a.cell_end[a.P - 1];
+            const float nan = __int_as_float(0x7fc00000);
+            for (int sl = nan0; sl < p.n_elec; ++sl) {
+                if ((sl - nan0) % (int)gridDim.x != (int)blockIdx.x) continue;
+                const size_t e = (size_t)p.perm[sl];
+                if (et == 0) {
+                    int bad = BLIP_STATUS_NONFINITE_POS;
+                    if (p.georec) bad |= p.georec[sl].bad;
+                    atomicOr(p.status, bad);
+                }
+                for (int l = et; l < p.Lreal; l += 32 * kEpiWarps) {
+                    p.values[e * L + l] = nan;
+                    if (!VONLY) {
+                        p.grads[e * 3 * L + l] = nan;
+                        p.grads[e * 3 * L + L + l] = nan;
+                        p.grads[e * 3 * L + 2 * L + l] = nan;
+                        p.laps[e * L + l] = nan;
+                    }
+                }
+            }
+        }
+        long long tile = 0;
+        for (long long part = 0;; ++part) {
+            const int wi = (int)(part & 1);
+            if (!wait_bar(w_full + wi, (unsigned)((part >> 1) & 1), abort_flag)) {
+                if (lane == 0) raise_abort(p, abort_flag);
+                break;
+            }
+            const int cnt = info[wi].cnt;
+            if (cnt < 0) break;
+            float *const *dst = info[wi].dst;
+            const int ncol = NO * cnt;
+            bool ok = true;
+            for (int m = 0; m < a.mt; ++m) {
+                const int ab = (int)(tile & 1);
+                if (!wait_bar(acc_full + ab, (unsigned)((tile >> 1) & 1), abort_flag)) {
+                    if (lane == 0) raise_abort(p, abort_flag);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int l = m * kMT + 32 * q + lane;
+                const bool in = l < p.Lreal;
+                const float sc = (p.scales && in) ? p.scales[l] : 1.0f;
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * kNmax);
+                for (int c0 = 32 * half; c0 < ncol; c0 += 64) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + c0, r);
+                    if (in) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj)
+                            if (c0 + jj < ncol) __stcs(dst[c0 + jj] + l, __uint_as_float(r[jj]) * sc);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty + ab);
+                ++tile;
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(epi_done + wi);
+        }
+    } else {
+        // ---------------- weights ----------------
+        // lane j = electron j of the part; weight warp ww writes the 4 stencil
+        // columns (kx, ky = ww), kx = 0..3.  Row r = NO j + o of the B operand
+        // sits 16 r bytes into a column's K group, so the 32 lanes of a store
+        // hit 32 different 16-byte slots (stride 80 or 16 bytes): no bank
+        // conflicts.
+        const int ww = warp - 2 - kEpiWarps;
+        bool ok = true;
+        long long part = 0;
+        // the info slot (and weight buffer) of a part is reused once the MMA
+        // thread and the epilogue have released the part that used it last
+        auto claim = [&]() -> bool {
+            const int wi = (int)(part & 1);
+            bool got = true;
+            if (part >= 2) {
+                const unsigned ph = (unsigned)(((part >> 1) - 1) & 1);
+                got = wait_bar(w_empty + wi, ph, abort_flag);
+                if (got) got = wait_bar(epi_done + wi, ph, abort_flag);
+            }
+            if (got && WB == 1 && part >= 1) {
+                // one weight buffer: the previous part's products must be done
+                const long long pp = part - 1;
+                got = wait_bar(w_empty + (int)(pp & 1), (unsigned)((pp >> 1) & 1), abort_flag);
+            }
+            if (!__all_sync(FULL, got) && lane == 0) raise_abort(p, abort_flag);
+            named_sync(1, 128);
+            return !*abort_flag;
+        };
+        const float *J = p.geo.J, *M = p.geo.M;
+        const float nrm = p.geo.norm;
+        for (int ci = blockIdx.x; ci < a.ncols && ok; ci += gridDim.x) {
+            const int k0 = a.cols[ci];
+            Cursor cur;
+            cursor_init(a, k0, cur);
+            int z0, s0, cnt;
+            while (next_part(a, k0, n3, cur, z0, s0, cnt)) {
+                if (!claim()) {
+                    ok = false;
+                    break;
+                }
+                const int wi = (int)(part & 1);
+                const int wb = WB == 2 ? wi : 0;
+                const int N = (NO * cnt + 15) & ~15;
+                const int j = lane;
+                // this lane's electron: geometry, 1-D factors
+                int cz = 0;
+                float X[4][3], Y[3], Z[4][3];
+                if (j < cnt) {
+                    const int slot = s0 + j;
+                    const int e = p.perm[slot];
+                    int i2, bad;
+                    float t0, t1, t2;
+                    if (p.georec) {
+                        const int4 gi = *reinterpret_cast<const int4 *>(p.georec + slot);
+                        const float4 gt = *reinterpret_cast<const float4 *>(&p.georec[slot].t[0]);
+                        i2 = gi.z;
+                        bad = gi.w;
+                        t0 = gt.x;
+                        t1 = gt.y;
+                        t2 = gt.z;
+                    } else {
+                        const double *rp = p.pos + 3 * (size_t)e;
+                        int i0, i1;
+                        bad = wrap_axis(p.geo, 0, rp[0], rp[1], rp[2], i0, t0);
+                        bad |= wrap_axis(p.geo, 1, rp[0], rp[1], rp[2], i1, t1);
+                        bad |= wrap_axis(p.geo, 2, rp[0], rp[1], rp[2], i2, t2);
+                    }
+                    // the sort put the electron in one of the part's cells; clamp
+                    // anyway so that every weight stays inside its 8-row window
+                    cz = min(max(i2 - z0, 0), kSegCells - 1);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        bspline_1d(t0, k, X[k][0], X[k][1], X[k][2]);
+                        bspline_1d(t2, k, Z[k][0], Z[k][1], Z[k][2]);
+                    }
+                    bspline_1d(t1, ww, Y[0], Y[1], Y[2]);
+                    if (ww == 0) {
+                        if (bad) atomicOr(p.status, bad);
+                        float **dst = info[wi].dst;
+                        const size_t L = (size_t)p.Lreal;
+                        if constexpr (VONLY) {
+                            dst[j] = p.values + (size_t)e * L;
+                        } else {
+                            dst[5 * j] = p.values + (size_t)e * L;
+                            dst[5 * j + 1] = p.grads + (size_t)e * 3 * L;
+                            dst[5 * j + 2] = p.grads + (size_t)e * 3 * L + L;
+                            dst[5 * j + 3] = p.grads + (size_t)e * 3 * L + 2 * L;
+                            dst[5 * j + 4] = p.laps + (size_t)e * L;
+                        }
+                    }
+                }
+                if (ww == 0 && lane == 0) {
+                    info[wi].cnt = cnt;
+                    info[wi].n = N;
+                }
+                unsigned char *wdst = wbuf + wb * Cfg::W_BUF;
+#pragma unroll
+                for (int kx = 0; kx < 4; ++kx) {
+                    const int c = 4 * kx + ww;
+                    // the 4 weights (kz = 0..3) of each output, 0 past cnt
+                    float w[NO][4];
+#pragma unroll
+                    for (int kz = 0; kz < 4; ++kz) {
+                        if (j < cnt) {
+                            const float X0 = X[kx][0], X1 = X[kx][1], X2 = X[kx][2];
+                            const float Z0 = Z[kz][0], Z1 = Z[kz][1], Z2 = Z[kz][2];
+                            w[0][kz] = nrm * (X0 * Y[0] * Z0);
+                            if constexpr (!VONLY) {
+                                const float gx = X1 * Y[0] * Z0, gy = X0 * Y[1] * Z0,
+                                            gz = X0 * Y[0] * Z1;
+                                w[1 % NO][kz] = nrm * (J[0] * gx + J[3] * gy + J[6] * gz);
+                                w[2 % NO][kz] = nrm * (J[1] * gx + J[4] * gy + J[7] * gz);
+                                w[3 % NO][kz] = nrm * (J[2] * gx + J[5] * gy + J[8] * gz);
+                                const float hxx = X2 * Y[0] * Z0, hyy = X0 * Y[2] * Z0,
+                                            hzz = X0 * Y[0] * Z2;
+                                const float hxy = X1 * Y[1] * Z0, hxz = X1 * Y[0] * Z1,
+                                            hyz = X0 * Y[1] * Z1;
+                                w[4 % NO][kz] = nrm * (M[0] * hxx + M[1] * hyy + M[2] * hzz +
+                                                       2.0f * (M[3] * hxy + M[4] * hxz + M[5] * hyz));
+                            }
+                        } else {
+#pragma unroll
+                            for (int o = 0; o < NO; ++o) w[o][kz] = 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int o = 0; o < NO; ++o) {
+                        const int r = NO * j + o;
+                        if (r < N) {
+                            // split into 16-bit planes; the 4 weights sit at
+                            // window rows cz .. cz + 3 of the 8-row chunk
+                            float rem[4] = {w[o][0], w[o][1], w[o][2], w[o][3]};
+#pragma unroll
+                            for (int pl = 0; pl < WPL; ++pl) {
+                                uint64_t v64 = 0;
+#pragma unroll
+                                for (int kz = 0; kz < 4; ++kz) {
+                                    const unsigned short bb = to_bits<T>(rem[kz]);
+                                    rem[kz] -= from_bits<T>(bb);
+                                    v64 |= (uint64_t)bb << (16 * kz);
+                                }
+                                const int sh = 16 * cz;
+                                const uint64_t lo = cz == 4 ? 0ull : v64 << sh;
+                                const uint64_t hi = cz == 0 ? 0ull : cz == 4 ? v64 : v64 >> (64 - sh);
+                                uint4 v;
+                                v.x = (uint32_t)lo;
+                                v.y = (uint32_t)(lo >> 32);
+                                v.z = (uint32_t)hi;
+                                v.w = (uint32_t)(hi >> 32);
+                                *reinterpret_cast<uint4 *>(wdst + pl * kPlaneW + (uint32_t)c * 2048u +
+                                                           (uint32_t)r * 16u) = v;
+                            }
+                        }
+                    }
+                }
+                // the tensor cores read the buffer through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                named_sync(1, 128);
+                if (ww == 0 && lane == 0) mbar_arrive(w_full + wi);
+                ++part;
+            }
+        }
+        // no more parts
+        if (ok && claim()) {
+            if (ww == 0 && lane == 0) {
+                info[part & 1].cnt = -1;
+                mbar_arrive(w_full + (int)(part & 1));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+template <typename T, int APL, bool VONLY>
+cudaError_t launch_tc_t(const EvalParams &p, const TcArgs &a, const CUtensorMap &tm, int sm_count,
+                        cudaStream_t stream)
+{
+    constexpr size_t smem = tc_smem<APL>();
+    static_assert(smem <= 227 * 1024, "stages and weight buffers exceed shared memory");
+    static bool attr_set = false;   // raise this instantiation's dynamic shared-memory cap once
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(blip_eval_tc<T, APL, VONLY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int grid = std::max(1, std::min(sm_count, a.ncols));
+    blip_eval_tc<T, APL, VONLY><<<grid, kThreads, smem, stream>>>(p, a, tm);
+    return cudaGetLastError();
+}
+
+template <typename T, int APL>
+cudaError_t launch_tc_v(const EvalParams &p, const TcArgs &a, const CUtensorMap &tm, int sm_count,
+                        cudaStream_t stream)
+{
+    return p.grads == nullptr ? launch_tc_t<T, APL, true>(p, a, tm, sm_count, stream)
+                              : launch_tc_t<T, APL, false>(p, a, tm, sm_count, stream);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+// Power-of-two scale of each component: the smallest 2^k >= max |a| (1 for
+// an all-zero component), from the max |a| bits of the FP32 table.
+__global__ void pow2_scales_kernel(const unsigned int *bits, int n, float *scales)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const float m = __uint_as_float(bits[l]);
+    int e = 0;
+    const float f = frexpf(m, &e);                      // m = f 2^e, f in [0.5, 1)
+    scales[l] = m > 0.0f ? ldexpf(1.0f, f == 0.5f ? e - 1 : e) : 1.0f;
+}
+
+// hi, lo FP16 planes [2][n] of an FP32 table (rows of row_stride
+// components): v = a / s_l (exact), hi = RN(v), lo = RN(v - hi).
+__global__ void split_pairs_kernel(const float *src, long long n, long long row_stride,
+                                   const float *scales, __half *dst)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float v = src[i] / scales[i % row_stride];
+        const __half h = __float2half_rn(v);
+        dst[i] = h;
+        dst[n + i] = __float2half_rn(v - __half2float(h));
+    }
+}
+
+}  // namespace
+
+cudaError_t make_tc_tmap(const void *base, int elem, long long row_stride, long long rows_total,
+                         TmaDesc *out)
+{
+    if (!out || row_stride < kMT || rows_total < 1 || (elem != ELEM_BF16 && elem != ELEM_F16))
+        return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tc_encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const CUtensorMapDataType dt =
+        elem == ELEM_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[2] = {(cuuint64_t)row_stride, (cuuint64_t)rows_total};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_stride * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)kWin};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap *>(out), dt, 2, const_cast<void *>(base), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_split_pairs(const float *src, long long rows, long long row_stride, int Lreal,
+                              unsigned int *bits, float *scales, void *dst, cudaStream_t stream)
+{
+    // padding components past Lreal are zero: their scale is 1
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned int) * (size_t)row_stride, stream);
+    if (e == cudaSuccess) e = launch_absmax(src, rows, row_stride, Lreal, bits, stream);
+    if (e == cudaSuccess) {
+        pow2_scales_kernel<<<(unsigned)((row_stride + 255) / 256), 256, 0, stream>>>(
+            bits, (int)row_stride, scales);
+        e = cudaGetLastError();
+    }
+    const long long n = rows * row_stride;
+    if (e == cudaSuccess) {
+        const long long blocks = std::min<long long>((n + 255) / 256, 65535LL * 8);
+        split_pairs_kernel<<<(unsigned)std::max<long long>(1, blocks), 256, 0, stream>>>(
+            src, n, row_stride, scales, static_cast<__half *>(dst));
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
+                      int ncols, long long plane_rows, const TmaDesc &tmap, int sm_count, int stall,
+                      cudaStream_t stream)
+{
+    if (!p.perm || !cell_end || !cols || ncols < 1 || p.n_k || plane_rows >= (1LL << 31))
+        return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.cell_end = cell_end;
+    a.cols = cols;
+    a.ncols = ncols;
+    a.P = (int)sort_key_count(p.geo);
+    a.mt = (p.Lreal + kMT - 1) / kMT;
+    a.plane_rows = (int)plane_rows;
+    a.stall = stall;
+    const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(&tmap);
+    switch (elem) {
+    case ELEM_F32: return launch_tc_v<__half, 2>(p, a, tm, sm_count, stream);
+    case ELEM_BF16: return launch_tc_v<__nv_bfloat16, 1>(p, a, tm, sm_count, stream);
+    case ELEM_F16: return launch_tc_v<__half, 1>(p, a, tm, sm_count, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace blip
