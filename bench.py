@@ -185,6 +185,16 @@ def sgemm_tflops(n=8192, reps=5):
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
+def tensor_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("bf16_tflops"):
+            return d["bf16_tflops"], "measured"
+    return 1900.0, "fallback"
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -433,25 +443,50 @@ def launch_model(mode, E, Lr, U, b_c):
     return U * Lr * b_c + out + 24.0 * E, fl
 
 
-def roofline(bytes_alg, flops, ms, sms):
+def tensor_products(kernel, storage):
+    """16-bit tensor-core products per algorithmic FMA of the tensor-core
+    kernel (variant 12): weights in two parts against a 16-bit table (2), or
+    against an FP32 table's two FP16 planes less the lo x lo term (3); 0 for
+    the CUDA-core kernels."""
+    if kernel is None or int(kernel[0]) != 12:
+        return 0
+    return 3 if storage in ("f32", "c64") else 2
+
+
+def roofline(bytes_alg, flops, ms, sms, products=0):
     """The binding roofline of one launch: HBM (measured copy bandwidth) or
-    the FP32 FMA pipe (SMs x 128 lanes x 2 FLOP x 2.07 GHz)."""
+    the arithmetic pipe the kernel contracts on: the FP32 FMA pipe (SMs x
+    128 lanes x 2 FLOP x 2.07 GHz) for the CUDA-core kernels; for the
+    tensor-core kernel the measured dense BF16 tensor peak (burst) with the
+    algorithmic FLOPs times the 16-bit products each FMA takes."""
     peak, peak_kind = measured_peaks()
     f32_peak = sms * 128 * 2 * 2.07e9 / 1e12
     t_hbm = bytes_alg / (peak * 1e9)
-    t_alu = flops / (f32_peak * 1e12)
     hbm_ach = bytes_alg / (ms / 1e3) / 1e9
     alu_ach = flops / (ms / 1e3) / 1e12
-    if t_hbm >= t_alu:
+    if products:
+        tc_peak, tc_kind = tensor_peak()
+        work = flops * products
+        t_cmp = work / (tc_peak * 1e12)
+        cmp = {"bound": "tensor", "achieved": work / (ms / 1e3) / 1e12, "peak": tc_peak,
+               "unit": "TFLOP/s", "frac": work / (ms / 1e3) / 1e12 / tc_peak,
+               "peak_kind": f"{tc_kind} dense BF16 tensor throughput (burst); "
+                            f"{products} 16-bit products per FMA"}
+    else:
+        t_cmp = flops / (f32_peak * 1e12)
+        cmp = {"bound": "alu", "achieved": alu_ach, "peak": f32_peak, "unit": "TFLOP/s",
+               "frac": alu_ach / f32_peak,
+               "peak_kind": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x 2.07 GHz"}
+    if t_hbm >= t_cmp:
         r = {"bound": "hbm", "achieved": hbm_ach, "peak": peak, "unit": "GB/s",
              "frac": hbm_ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
     else:
-        r = {"bound": "alu", "achieved": alu_ach, "peak": f32_peak, "unit": "TFLOP/s",
-             "frac": alu_ach / f32_peak,
-             "peak_kind": f"FP32 FMA: {sms} SMs x 128 lanes x 2 FLOP x 2.07 GHz"}
+        r = cmp
     r.update({"algorithmic_bytes_per_launch": bytes_alg, "fp32_flop_per_launch": flops,
               "hbm_frac": hbm_ach / peak, "alu_frac": alu_ach / f32_peak,
-              "roof_time_us": 1e6 * max(t_hbm, t_alu)})
+              "roof_time_us": 1e6 * max(t_hbm, t_cmp)})
+    if products:
+        r["tensor_frac"] = cmp["frac"]
     return r
 
 
@@ -581,11 +616,18 @@ def main():
     U = touched_sites(w.grid, w.lattice, pos)
     b_c = ELEM_BYTES[args.storage]
     bytes_alg, flops = launch_model("full", E, Lr, U, b_c)
-    roof = roofline(bytes_alg, flops, ms, sms)
+    roof = roofline(bytes_alg, flops, ms, sms, tensor_products(chosen, args.storage))
     kh = kernel_hash()
     roof["traffic"] = NCU_TRAFFIC.get((kh, w.name, args.storage, E), {}).get(tuple(chosen[:2]))
     roof.update({"touched_sites": U, "kernel_source_hash": kh,
                  "gather_model_GBps": (E * 64 * Lr * b_c + 20 * Lr * E) / (ms / 1e3) / 1e9})
+    if not args.no_probe and roof["bound"] == "hbm" and E * Lr * 20 > 4e9:
+        # the output stream's own ceiling: a plain write of the gradient
+        # buffer (12 of the launch's 20 L bytes per electron), timed alike
+        g = out[1]
+        wms = statistics.mean(st_.time(lambda: g.fill_(0.5), max(3, K // 4)))
+        roof["hbm_write_probe_GBps"] = g.numel() * 4 / (wms / 1e3) / 1e9
+        roof["frac_of_write_probe"] = roof["achieved"] / roof["hbm_write_probe_GBps"]
     if roof["bound"] == "alu" and not args.no_probe:
         sg = sgemm_tflops()
         roof["fp32_sgemm_tflops"] = sg
@@ -653,10 +695,10 @@ def main():
     return 0
 
 
-def _timed_entry(ms_list, E, Lr, U, b_c, mode, sms, chosen=None):
+def _timed_entry(ms_list, E, Lr, U, b_c, mode, sms, chosen=None, storage="f32"):
     ms = statistics.mean(ms_list)
     bytes_alg, flops = launch_model(mode, E, Lr, U, b_c)
-    r = roofline(bytes_alg, flops, ms, sms)
+    r = roofline(bytes_alg, flops, ms, sms, tensor_products(chosen, storage))
     d = {"us": 1e3 * ms, "evals_per_s": E * Lr / (ms / 1e3), "bound": r["bound"],
          "frac": r["frac"], "hbm_frac": r["hbm_frac"], "alu_frac": r["alu_frac"],
          "roof_us": r["roof_time_us"]}
@@ -681,12 +723,14 @@ def extras_precision(args, pb, w, tab, pos, dpos, doffs, t32, out, st_, line, sm
     for storage in ("f32", "bf16", "f16"):
         if storage == "f32":
             t = t32
-            ent = _timed_entry([ms32], E, Lr, U, 4, "full", sms, chosen32)
+            ent = _timed_entry([ms32], E, Lr, U, 4, "full", sms, chosen32, "f32")
+            t.eval(dpos, doffs, out=out)          # the outputs again (the write probe used them)
+            torch.cuda.synchronize()
         else:
             t = pb.BlipTable(w.grid, w.lattice, tab, storage=STORAGE[storage])
             ch = t.autotune(dpos, doffs, out=out)
             ent = _timed_entry(st_.time(lambda: t.eval(dpos, doffs, out=out), K), E, Lr, U,
-                               ELEM_BYTES[storage], "full", sms, ch)
+                               ELEM_BYTES[storage], "full", sms, ch, storage)
             t.eval(dpos, doffs, out=out)
             torch.cuda.synchronize()
         rows = [out[0][idx].cpu().numpy(), out[1][idx].cpu().numpy(), out[2][idx].cpu().numpy()]
@@ -711,7 +755,8 @@ def extras_precision(args, pb, w, tab, pos, dpos, doffs, t32, out, st_, line, sm
         o1 = (out[0], None, None)
         ch = t.autotune(dpos, doffs, values_only=True, out=o1)
         vo[storage] = _timed_entry(st_.time(lambda: t.eval(dpos, doffs, values_only=True, out=o1),
-                                            K), E, Lr, U, ELEM_BYTES[storage], "vonly", sms, ch)
+                                            K), E, Lr, U, ELEM_BYTES[storage], "vonly", sms, ch,
+                                   storage)
     line["values_only"] = vo
     cols = out[1].view(-1)[:E * Lr].view(E, Lr)          # any float data will do for timing
     ra = {}
@@ -740,7 +785,7 @@ def extras_precision(args, pb, w, tab, pos, dpos, doffs, t32, out, st_, line, sm
             t = tables[storage]
             ch = t.autotune(db, dob, out=ob_)
             ent = _timed_entry(st_.time(lambda: t.eval(db, dob, out=ob_), K), Eb, Lr, Ub,
-                               ELEM_BYTES[storage], "full", sms, ch)
+                               ELEM_BYTES[storage], "full", sms, ch, storage)
             ent.update({"b": b, "E": Eb, "storage": storage})
             sweep.append(ent)
     line["batch_sweep"] = sweep

@@ -66,6 +66,8 @@ struct blip_table_s {
     void *d_planes = nullptr;
     float *d_tc_scales = nullptr;
     TmaDesc tc_tmap = {};
+    TmaDesc tc_tmap5 = {};
+    bool tc_wide = false;
     bool tc_ready = false;
     // Bloch k-points (complex tables)
     int n_k = 0;
@@ -302,8 +304,12 @@ int tc_prepare(blip_table_s *t)
         operand = t->d_planes;
         rows_total = 2 * t->rows;
     }
-    CK(make_tc_tmap(operand, t->elem == ELEM_F32 ? ELEM_F16 : t->elem, t->row_stride, rows_total,
-                    &t->tc_tmap));
+    const int op_elem = t->elem == ELEM_F32 ? ELEM_F16 : t->elem;
+    CK(make_tc_tmap(operand, op_elem, t->row_stride, rows_total, &t->tc_tmap));
+    // the 5-D view for 8 KB boxes; without it the kernel uses 1 KB boxes only
+    t->tc_wide = make_tc_tmap5(operand, op_elem, t->row_stride, t->grid[0] * t->grid[1],
+                               t->grid[2], t->elem == ELEM_F32 ? 2 : 1, t->rows,
+                               &t->tc_tmap5) == cudaSuccess;
     t->tc_ready = true;
     return BLIP_OK;
 }
@@ -371,8 +377,8 @@ int launch_choice(blip_table_s *t, const EvalParams &p, const KernelChoice &kc, 
         sort_views(t->geo, p.n_elec, scratch, &keys, &cell_end);
         EvalParams pt = p;
         if (t->elem == ELEM_F32) pt.scales = t->d_tc_scales;   // the planes' power-of-two scales
-        CK(launch_tc(pt, t->elem, cell_end, t->d_cols, t->ncols, t->rows, t->tc_tmap, t->sm_count,
-                     t->test_stall, stream));
+        CK(launch_tc(pt, t->elem, cell_end, t->d_cols, t->ncols, t->rows, t->tc_tmap,
+                     t->tc_wide ? &t->tc_tmap5 : nullptr, t->sm_count, t->test_stall, stream));
     } else if (kc.variant == VAR_SPLIT) {
         CK(launch_split(p, t->elem, stream));
     } else if (kc.variant == VAR_REGISTER_PERSIST) {

@@ -194,10 +194,16 @@ cudaError_t launch_split_pairs(const float *src, long long rows, long long row_s
 // Launch the tensor-core kernel (needs the sort): elem = ELEM_BF16 / ELEM_F16
 // (tmap over the table, p.scales its per-component scales or null) or ELEM_F32
 // (tmap over its two FP16 planes, each plane_rows rows, p.scales their
-// power-of-two scales); cols: the ncols column keys in sort order.
+// power-of-two scales); tmap5: the 5-D view (or null: 1 KB boxes only);
+// cols: the ncols column keys in sort order.
+// The 5-D view of the same operand for 8 KB boxes: components within a
+// 64-component slab, rows of a grid column (n3 + 3), grid columns (n1 n2),
+// slabs, planes; box 64 x 8 x 4 x 2 x 1.
+cudaError_t make_tc_tmap5(const void *base, int elem, long long row_stride, int n12, int n3,
+                          int planes, long long plane_rows, TmaDesc *out);
 cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
-                      int ncols, long long plane_rows, const TmaDesc &tmap, int sm_count, int stall,
-                      cudaStream_t stream);
+                      int ncols, long long plane_rows, const TmaDesc &tmap, const TmaDesc *tmap5,
+                      int sm_count, int stall, cudaStream_t stream);
 
 // Launch the split-stencil kernel: a block of 4 warps per (electron, chunk),
 // warp q contracting the 16 sites of a_1 slab q, partial sums added in a

@@ -25,11 +25,13 @@
 // accumulated in FP32 in tensor memory.
 //
 // Persistent grid, one CTA per SM, 14 warps:
-//   warp 0      TMA producer: per (part, M tile) the 16 columns x 2 orbital
-//               halves of 8 rows x 64 components (one 128-byte-swizzled
-//               1 KB box each, per plane) into a 3-stage ring;
+//   warp 0      TMA producer: per (part, M tile, plane) the 16 stencil
+//               columns x 2 halves of 8 rows x 64 components into a 3-stage
+//               ring, as 4 boxes of 8 KB (4 consecutive grid columns x 2
+//               halves, a 5-D view of the table) or, where the columns wrap
+//               around the cell, 32 boxes of 1 KB;
 //   warp 1      allocates tensor memory and issues the MMAs (one thread):
-//               per M tile, 8 K steps x planes products into one of two
+//               per M tile, 8 K steps x planes products into one of four
 //               128-column FP32 accumulators, then tcgen05.commit to the
 //               stage's empty barrier and the accumulator's full barrier;
 //   warps 2-9   epilogue, two warps per lane quarter of the accumulator:
@@ -70,19 +72,28 @@ constexpr int kEpiWarps = 8;           // two per tensor-memory lane quarter
 constexpr int kThreads = 32 * (2 + kEpiWarps + 4);
 constexpr uint32_t kBox = 1024;                          // 8 rows x 128 bytes
 constexpr uint32_t kStage = kMT * kK * 2;                // one operand plane of one M tile: 32 KB
-constexpr uint32_t kPlaneW = kNmax * kK * 2;             // one weight plane: 32 KB
-constexpr uint32_t kTmemCols = 256;                      // two 128-column accumulators
+constexpr uint32_t kTmemCols = 512;                      // all of tensor memory
 
 // Shapes of one instantiation: APL coefficient planes per M tile (1: the
 // 16-bit table as stored; 2: an FP32 table as two FP16 planes, hi + lo, of
-// the coefficient over a power-of-two per-component scale), two 16-bit weight
-// planes (hi + lo) in two buffers (the next part's weights are built while
-// the current part's products run), a ring of 3 operand stages.
-template <int APL> struct TcCfg {
-    static constexpr int WPL = 2;
+// the coefficient over a power-of-two per-component scale); the weights in
+// two 16-bit parts stacked along N in one B operand (rows [0, RLO) the hi
+// part of the part's NO x cnt rows, rows [RLO, 2 RLO) the lo part; RLO = 128
+// with five outputs, 32 values only), so that one product of N = RLO + NH
+// covers both (an M = 128, K = 16 product costs the same for any N up to
+// 256: measured 150 cycles); two buffers of it (the next part's weights are
+// built while the current part's products run); as many 32 KB operand
+// stages as the rest of shared memory holds; accumulators of 2 RLO columns
+// (hi, then lo products), as many as tensor memory holds (at most 4).
+template <int APL, bool VONLY> struct TcCfg {
+    static constexpr int RLO = VONLY ? 32 : kNmax;
+    static constexpr int WROWS = 2 * RLO;
+    static constexpr uint32_t KGROUP = WROWS * 16;           // bytes per K group (8 rows of K)
+    static constexpr uint32_t W_BUF = KGROUP * kCols;        // the stacked B operand
     static constexpr int WB = 2;
-    static constexpr int STAGES = 3;
-    static constexpr uint32_t W_BUF = WPL * kPlaneW;
+    static constexpr int STAGES = (int)((229376u - WB * W_BUF) / kStage);
+    static constexpr int ACC_COLS = 2 * RLO;
+    static constexpr int NACC = (int)(kTmemCols / ACC_COLS) > 4 ? 4 : (int)(kTmemCols / ACC_COLS);
 };
 
 // Part bookkeeping shared by the weight warps (writers), the MMA thread and
@@ -102,13 +113,14 @@ struct TcArgs {
     int mt;                // M tiles (ceil(Lreal / 128))
     int plane_rows;        // rows of one coefficient plane in the tensor map
     int stall;             // test hook: the MMA thread never releases the first stage
+    int wide;              // 1: the 5-D tensor map (8 KB boxes) is usable
 };
 
-template <int APL>
+template <int APL, bool VONLY>
 constexpr size_t tc_smem()
 {
-    return TcCfg<APL>::STAGES * kStage +
-           TcCfg<APL>::WB * TcCfg<APL>::W_BUF + 2 * sizeof(PartInfo) + 256;
+    using C = TcCfg<APL, VONLY>;
+    return C::STAGES * kStage + C::WB * C::W_BUF + 2 * sizeof(PartInfo) + 256;
 }
 
 // ---------------------------------------------------------------------------
@@ -155,7 +167,7 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // 32 consecutive accumulator columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
 {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
@@ -166,7 +178,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+
+// Tiled tensor copy of one 5-D box at element coordinates (c0 .. c4).
+__device__ __forceinline__ void tma_load_5d(void *dst, const void *tmap, int c0, int c1, int c2,
+                                            int c3, int c4, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void named_sync(int id, int threads)
@@ -195,6 +218,30 @@ __device__ __forceinline__ void raise_abort(const EvalParams &p, volatile int *a
 // parts: the same deterministic walk for the producer and the weight warps
 // ---------------------------------------------------------------------------
 
+// Cell counts of one grid column, read by a whole warp: lane i holds
+// cell_end[k0 + base + i] (one coalesced load per 32 cells), and the walk
+// reads them by shuffle, so the part walk has no chain of dependent loads.
+struct ColumnEnds {
+    int k0, base, val;
+};
+
+__device__ __forceinline__ void ends_init(const TcArgs &a, int k0, int n3, int lane, ColumnEnds &w)
+{
+    w.k0 = k0;
+    w.base = 0;
+    w.val = lane < n3 ? a.cell_end[k0 + lane] : 0;
+}
+
+// cell_end[k0 + z]; every lane of the warp calls it with the same z
+__device__ __forceinline__ int ends_at(const TcArgs &a, int n3, int lane, ColumnEnds &w, int z)
+{
+    if (z < w.base || z >= w.base + 32) {
+        w.base = z;
+        w.val = z + lane < n3 ? a.cell_end[w.k0 + z + lane] : 0;
+    }
+    return __shfl_sync(FULL, w.val, z - w.base);
+}
+
 struct Cursor {
     int z;        // current cell along a_3
     int used;     // electrons of cell z already in earlier parts
@@ -208,16 +255,16 @@ __device__ __forceinline__ void cursor_init(const TcArgs &a, int k0, Cursor &c)
     c.sbase = k0 ? a.cell_end[k0 - 1] : 0;
 }
 
-// Next part of the column whose cell (x, y, 0) has key k0: up to kNE
-// electrons from at most kSegCells consecutive cells, starting at the first
-// cell with electrons left; a cell with more than kNE electrons gives parts
-// of kNE of its own.  Returns false when the column is done.
-__device__ __forceinline__ bool next_part(const TcArgs &a, int k0, int n3, Cursor &c, int &z0,
-                                          int &s0, int &cnt)
+// Next part of the column: up to kNE electrons from at most kSegCells
+// consecutive cells, starting at the first cell with electrons left; a cell
+// with more than kNE electrons gives parts of kNE of its own.  Returns false
+// when the column is done.  Called by every lane of a warp alike.
+__device__ __forceinline__ bool next_part(const TcArgs &a, int n3, int lane, ColumnEnds &w,
+                                          Cursor &c, int &z0, int &s0, int &cnt)
 {
     for (;;) {
         if (c.z >= n3) return false;
-        const int end = a.cell_end[k0 + c.z];
+        const int end = ends_at(a, n3, lane, w, c.z);
         if (end - c.sbase - c.used > 0) break;
         c.sbase = end;
         c.used = 0;
@@ -225,7 +272,7 @@ __device__ __forceinline__ bool next_part(const TcArgs &a, int k0, int n3, Curso
     }
     z0 = c.z;
     s0 = c.sbase + c.used;
-    const int end0 = a.cell_end[k0 + c.z];
+    const int end0 = ends_at(a, n3, lane, w, c.z);
     if (end0 - s0 >= kNE) {
         cnt = kNE;
         c.used += kNE;
@@ -236,7 +283,7 @@ __device__ __forceinline__ bool next_part(const TcArgs &a, int k0, int n3, Curso
     c.used = 0;
     ++c.z;
     while (c.z < n3 && c.z < z0 + kSegCells) {
-        const int e = a.cell_end[k0 + c.z];
+        const int e = ends_at(a, n3, lane, w, c.z);
         if (cnt + (e - c.sbase) > kNE) break;
         cnt += e - c.sbase;
         c.sbase = e;
@@ -283,10 +330,11 @@ template <> __device__ __forceinline__ float from_bits<__half>(unsigned short b)
 // 2: an FP32 table as two scaled FP16 planes).
 template <typename T, int APL, bool VONLY>
 __global__ void __launch_bounds__(kThreads, 1)
-    blip_eval_tc(EvalParams p, TcArgs a, const __grid_constant__ CUtensorMap tmap)
+    blip_eval_tc(EvalParams p, TcArgs a, const __grid_constant__ CUtensorMap tmap,
+                 const __grid_constant__ CUtensorMap tmap5)
 {
-    using Cfg = TcCfg<APL>;
-    constexpr int WPL = Cfg::WPL, WB = Cfg::WB, NS = Cfg::STAGES;
+    using Cfg = TcCfg<APL, VONLY>;
+    constexpr int WPL = 2, WB = Cfg::WB, NS = Cfg::STAGES;    // WPL: weight parts (hi, lo)
     constexpr int NO = VONLY ? 1 : 5;                    // outputs per electron
     constexpr int FMT = std::is_same<T, __nv_bfloat16>::value ? 1 : 0;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -302,7 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(info + 2);
     uint64_t *a_full = bars, *a_empty = bars + NS;
     uint64_t *w_full = bars + 2 * NS, *w_empty = w_full + 2, *epi_done = w_full + 4;
-    uint64_t *acc_full = w_full + 6, *acc_empty = w_full + 8, *drain = w_full + 10;
+    constexpr int kAcc = Cfg::NACC;
+    uint64_t *acc_full = w_full + 6, *acc_empty = acc_full + kAcc, *drain = acc_empty + kAcc;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -318,6 +367,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(w_full + b, 1);
             mbar_init(w_empty + b, 1);
             mbar_init(epi_done + b, kEpiWarps);
+        }
+        for (int b = 0; b < kAcc; ++b) {
             mbar_init(acc_full + b, 1);
             mbar_init(acc_empty + b, kEpiWarps);
         }
@@ -341,13 +392,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- TMA producer ----------------
         long long fill = 0;
         bool ok = true;
-        // this lane's box: stencil column c = lane / 2, orbital half lane % 2
-        const int c = lane >> 1, h = lane & 1;
+        // stage layout: stencil column (kx, ky), component half h at
+        // kx 8 KB + h 4 KB + ky 1 KB (one 128-byte-swizzled 8-row atom each)
+        const int c = lane >> 1, h = lane & 1;     // narrow boxes: column c, half h
+        const int kxl = c >> 2, kyl = c & 3;
         for (int ci = blockIdx.x; ci < a.ncols && ok; ci += gridDim.x) {
             const int k0 = a.cols[ci];
             int x, y;
             column_xy(p.geo, k0, x, y);
-            int gx = x - 1 + (c >> 2), gy = y - 1 + (c & 3);
+            // the 4 stencil columns y - 1 .. y + 2 of one kx are consecutive in
+            // memory unless they wrap around the cell: then one 8 KB box per kx
+            // (5-D view), else 1 KB boxes
+            const bool wide = a.wide && y >= 1 && y + 2 < n2;
+            int gx = x - 1 + (wide ? lane : kxl), gy = y - 1 + kyl;
             gx += gx < 0 ? p.geo.n[0] : 0;
             gx -= gx >= p.geo.n[0] ? p.geo.n[0] : 0;
             gy += gy < 0 ? n2 : 0;
@@ -355,10 +412,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int colrow = (gx * n2 + gy) * (n3 + 3);
             Cursor cur;
             cursor_init(a, k0, cur);
+            ColumnEnds ends;
+            ends_init(a, k0, n3, lane, ends);
             int z0, s0, cnt;
-            while (ok && next_part(a, k0, n3, cur, z0, s0, cnt)) {
+            while (ok && next_part(a, n3, lane, ends, cur, z0, s0, cnt)) {
                 for (int m = 0; m < a.mt && ok; ++m)
-                    for (int pl = APL - 1; pl >= 0; --pl) {      // FP32: lo, mid, hi
+                    for (int pl = 0; pl < APL; ++pl) {           // FP32: hi, then lo
                         const int s = (int)(fill % NS);
                         const long long k = fill / NS;
                         if (k > 0) {
@@ -371,8 +430,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         if (lane == 0) mbar_expect_tx(a_full + s, kStage);
                         __syncwarp();
-                        tma_load_2d(stageA + s * kStage + c * kBox + h * (kStage / 2), &tmap,
-                                    m * kMT + 64 * h, pl * a.plane_rows + colrow + z0, a_full + s);
+                        unsigned char *st = stageA + s * kStage;
+                        if (wide) {
+                            if (lane < 4)
+                                tma_load_5d(st + lane * 8192, &tmap5, 0, z0, gx * n2 + y - 1, 2 * m, pl,
+                                            a_full + s);
+                        } else {
+                            tma_load_2d(st + kxl * 8192 + h * 4096 + kyl * kBox, &tmap,
+                                        m * kMT + 64 * h, pl * a.plane_rows + colrow + z0, a_full + s);
+                        }
                         ++fill;
                     }
             }
@@ -395,20 +461,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             if (info[wi].cnt < 0) break;
-            const uint32_t id = instr_desc(info[wi].n, FMT);
+            const int nh = info[wi].n;                       // rows of one weight part
+            const uint32_t id_both = instr_desc(Cfg::RLO + nh, FMT);   // hi and lo parts
+            const uint32_t id_hi = instr_desc(nh, FMT);                 // hi part only
             const uint32_t sw = w_base + wb * Cfg::W_BUF;
             for (int m = 0; m < a.mt && ok; ++m) {
-                const int ab = (int)(tile & 1);
-                if (tile >= 2) {
-                    const bool got = wait_bar(acc_empty + ab, (unsigned)(((tile >> 1) - 1) & 1), abort_flag);
+                const int ab = (int)(tile % kAcc);
+                if (tile >= kAcc) {
+                    const bool got = wait_bar(acc_empty + ab, (unsigned)(((tile / kAcc) - 1) & 1), abort_flag);
                     if (!__all_sync(FULL, got)) {
                         if (lane == 0) raise_abort(p, abort_flag);
                         ok = false;
                         break;
                     }
                 }
-                const uint32_t d = tmem + (uint32_t)(ab * kNmax);
-                for (int pl = APL - 1; pl >= 0; --pl) {
+                const uint32_t d = tmem + (uint32_t)(ab * Cfg::ACC_COLS);
+                // the hi plane first: its product (N = RLO + NH) sets every
+                // column the epilogue reads; the lo plane's (N = NH) adds
+                for (int pl = 0; pl < APL; ++pl) {
                     const int s = (int)(fill % NS);
                     const bool got = wait_bar(a_full + s, (unsigned)((fill / NS) & 1), abort_flag);
                     if (!__all_sync(FULL, got)) {
@@ -419,25 +489,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     if (lane == 0) {
                         const uint32_t sa = stage_base + s * kStage;
-                        // a 16-bit table (pl = 0) meets both weight planes; of
-                        // an FP32 table's planes the lo one meets the hi weights
-                        // only (lo x lo is below 2^-22 relative)
-                        const int nw = APL == 1 ? WPL : 2 - pl;
+                        // a 16-bit table (pl = 0) meets both weight parts in one
+                        // product; of an FP32 table's planes the lo one meets the
+                        // hi weights only (lo x lo is below 2^-22 relative)
+                        const uint32_t id = (APL == 2 && pl == 1) ? id_hi : id_both;
 #pragma unroll 1
                         for (int ks = 0; ks < kK / 16; ++ks) {
-                            // A: 2 stencil columns (16 rows) per K step, 1 KB per
-                            // column, the second 64-component half kStage/2 on;
-                            // B: K groups of 8 at 2 KB, N groups of 8 rows at 128 B
-                            const uint64_t ad = smem_desc(sa + ks * 2 * kBox, kStage / 2, kBox, 2);
-                            for (int pw = 0; pw < nw; ++pw) {
-                                const uint64_t bd = smem_desc(sw + pw * kPlaneW + ks * 2 * 2048u,
-                                                              2048u, 128u, 0);
-                                const bool first = pl == APL - 1 && ks == 0 && pw == 0;
-                                mma_f16(d, ad, bd, id, first ? 0u : 1u);
-                            }
+                            // A: K step ks = stencil columns (kx, ky), (kx, ky + 1)
+                            // with kx = ks / 2, ky = 2 (ks % 2): 1 KB apart, the
+                            // second 64-component half 4 KB on; B: K groups of 8
+                            // at KGROUP bytes, N groups of 8 rows at 128 B
+                            const uint64_t ad = smem_desc(sa + (ks >> 1) * 8192 + (ks & 1) * 2 * kBox,
+                                                          4096u, kBox, 2);
+                            const uint64_t bd = smem_desc(sw + ks * 2 * Cfg::KGROUP, Cfg::KGROUP, 128u, 0);
+                            mma_f16(d, ad, bd, id, (pl == 0 && ks == 0) ? 0u : 1u);
                         }
                         if (!(a.stall && fill == 0)) mma_commit(a_empty + s);
-                        if (pl == 0) {
+                        if (pl == APL - 1) {
                             mma_commit(acc_full + ab);
                             if (m == a.mt - 1) mma_commit(w_empty + wi);
                         }
@@ -499,8 +567,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ncol = NO * cnt;
             bool ok = true;
             for (int m = 0; m < a.mt; ++m) {
-                const int ab = (int)(tile & 1);
-                if (!wait_bar(acc_full + ab, (unsigned)((tile >> 1) & 1), abort_flag)) {
+                const int ab = (int)(tile % kAcc);
+                if (!wait_bar(acc_full + ab, (unsigned)((tile / kAcc) & 1), abort_flag)) {
                     if (lane == 0) raise_abort(p, abort_flag);
                     ok = false;
                     break;
@@ -509,14 +577,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int l = m * kMT + 32 * q + lane;
                 const bool in = l < p.Lreal;
                 const float sc = (p.scales && in) ? p.scales[l] : 1.0f;
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * kNmax);
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) +
+                                       (uint32_t)(ab * Cfg::ACC_COLS);
                 for (int c0 = 32 * half; c0 < ncol; c0 += 64) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + c0, r);
+                    // the hi-part products in column c, the lo-part ones RLO on
+                    uint32_t r[32], rl[32];
+                    tmem_ld32_nowait(taddr + c0, r);
+                    tmem_ld32_nowait(taddr + Cfg::RLO + c0, rl);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (in) {
 #pragma unroll
                         for (int jj = 0; jj < 32; ++jj)
-                            if (c0 + jj < ncol) __stcs(dst[c0 + jj] + l, __uint_as_float(r[jj]) * sc);
+                            if (c0 + jj < ncol)
+                                __stcs(dst[c0 + jj] + l,
+                                       (__uint_as_float(r[jj]) + __uint_as_float(rl[jj])) * sc);
                     }
                 }
                 tc_fence_before();
@@ -532,9 +606,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- weights ----------------
         // lane j = electron j of the part; weight warp ww writes the 4 stencil
         // columns (kx, ky = ww), kx = 0..3.  Row r = NO j + o of the B operand
-        // sits 16 r bytes into a column's K group, so the 32 lanes of a store
-        // hit 32 different 16-byte slots (stride 80 or 16 bytes): no bank
-        // conflicts.
+        // (plus RLO for the lo part) sits 16 r bytes into a column's K group,
+        // so the 32 lanes of a store hit 32 different 16-byte slots (stride 80
+        // or 16 bytes): no bank conflicts.
         const int ww = warp - 2 - kEpiWarps;
         bool ok = true;
         long long part = 0;
@@ -559,12 +633,52 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         const float *J = p.geo.J, *M = p.geo.M;
         const float nrm = p.geo.norm;
-        for (int ci = blockIdx.x; ci < a.ncols && ok; ci += gridDim.x) {
-            const int k0 = a.cols[ci];
-            Cursor cur;
-            cursor_init(a, k0, cur);
-            int z0, s0, cnt;
-            while (next_part(a, k0, n3, cur, z0, s0, cnt)) {
+        // the parts of this CTA's columns in order, one part ahead: the next
+        // part's electron records are loaded while this part's weights are
+        // built (their latency was the weight warps' main cost)
+        int ci = blockIdx.x;
+        Cursor cur;
+        ColumnEnds ends;
+        if (ci < a.ncols) {
+            cursor_init(a, a.cols[ci], cur);
+            ends_init(a, a.cols[ci], n3, lane, ends);
+        }
+        auto advance = [&](int &z0_, int &s0_, int &cnt_) -> bool {
+            while (ci < a.ncols) {
+                if (next_part(a, n3, lane, ends, cur, z0_, s0_, cnt_)) return true;
+                ci += gridDim.x;
+                if (ci < a.ncols) {
+                    cursor_init(a, a.cols[ci], cur);
+                    ends_init(a, a.cols[ci], n3, lane, ends);
+                }
+            }
+            return false;
+        };
+        struct Rec {
+            int e;
+            int4 gi;
+            float4 gt;
+        };
+        auto load_rec = [&](int s0_, int cnt_, Rec &r) {
+            if (lane < cnt_) {
+                const int slot = s0_ + lane;
+                r.e = p.perm[slot];
+                if (p.georec) {
+                    r.gi = *reinterpret_cast<const int4 *>(p.georec + slot);
+                    r.gt = *reinterpret_cast<const float4 *>(&p.georec[slot].t[0]);
+                }
+            }
+        };
+        int nz0 = 0, ns0 = 0, ncnt = 0;
+        Rec nrec{};
+        bool have = advance(nz0, ns0, ncnt);
+        if (have) load_rec(ns0, ncnt, nrec);
+        while (have && ok) {
+            const int z0 = nz0, cnt = ncnt;
+            const Rec rec = nrec;
+            have = advance(nz0, ns0, ncnt);
+            if (have) load_rec(ns0, ncnt, nrec);
+            {
                 if (!claim()) {
                     ok = false;
                     break;
@@ -577,18 +691,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int cz = 0;
                 float X[4][3], Y[3], Z[4][3];
                 if (j < cnt) {
-                    const int slot = s0 + j;
-                    const int e = p.perm[slot];
+                    const int e = rec.e;
                     int i2, bad;
                     float t0, t1, t2;
                     if (p.georec) {
-                        const int4 gi = *reinterpret_cast<const int4 *>(p.georec + slot);
-                        const float4 gt = *reinterpret_cast<const float4 *>(&p.georec[slot].t[0]);
-                        i2 = gi.z;
-                        bad = gi.w;
-                        t0 = gt.x;
-                        t1 = gt.y;
-                        t2 = gt.z;
+                        i2 = rec.gi.z;
+                        bad = rec.gi.w;
+                        t0 = rec.gt.x;
+                        t1 = rec.gt.y;
+                        t2 = rec.gt.z;
                     } else {
                         const double *rp = p.pos + 3 * (size_t)e;
                         int i0, i1;
@@ -678,8 +789,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 v.y = (uint32_t)(lo >> 32);
                                 v.z = (uint32_t)hi;
                                 v.w = (uint32_t)(hi >> 32);
-                                *reinterpret_cast<uint4 *>(wdst + pl * kPlaneW + (uint32_t)c * 2048u +
-                                                           (uint32_t)r * 16u) = v;
+                                *reinterpret_cast<uint4 *>(wdst + (uint32_t)c * Cfg::KGROUP +
+                                                           (uint32_t)(r + pl * Cfg::RLO) * 16u) = v;
                             }
                         }
                     }
@@ -710,10 +821,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <typename T, int APL, bool VONLY>
-cudaError_t launch_tc_t(const EvalParams &p, const TcArgs &a, const CUtensorMap &tm, int sm_count,
-                        cudaStream_t stream)
+cudaError_t launch_tc_t(const EvalParams &p, const TcArgs &a, const CUtensorMap &tm,
+                        const CUtensorMap &tm5, int sm_count, cudaStream_t stream)
 {
-    constexpr size_t smem = tc_smem<APL>();
+    constexpr size_t smem = tc_smem<APL, VONLY>();
     static_assert(smem <= 227 * 1024, "stages and weight buffers exceed shared memory");
     static bool attr_set = false;   // raise this instantiation's dynamic shared-memory cap once
     if (!attr_set) {
@@ -723,16 +834,16 @@ cudaError_t launch_tc_t(const EvalParams &p, const TcArgs &a, const CUtensorMap 
         attr_set = true;
     }
     const int grid = std::max(1, std::min(sm_count, a.ncols));
-    blip_eval_tc<T, APL, VONLY><<<grid, kThreads, smem, stream>>>(p, a, tm);
+    blip_eval_tc<T, APL, VONLY><<<grid, kThreads, smem, stream>>>(p, a, tm, tm5);
     return cudaGetLastError();
 }
 
 template <typename T, int APL>
-cudaError_t launch_tc_v(const EvalParams &p, const TcArgs &a, const CUtensorMap &tm, int sm_count,
-                        cudaStream_t stream)
+cudaError_t launch_tc_v(const EvalParams &p, const TcArgs &a, const CUtensorMap &tm,
+                        const CUtensorMap &tm5, int sm_count, cudaStream_t stream)
 {
-    return p.grads == nullptr ? launch_tc_t<T, APL, true>(p, a, tm, sm_count, stream)
-                              : launch_tc_t<T, APL, false>(p, a, tm, sm_count, stream);
+    return p.grads == nullptr ? launch_tc_t<T, APL, true>(p, a, tm, tm5, sm_count, stream)
+                              : launch_tc_t<T, APL, false>(p, a, tm, tm5, sm_count, stream);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn()
@@ -796,6 +907,31 @@ cudaError_t make_tc_tmap(const void *base, int elem, long long row_stride, long 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t make_tc_tmap5(const void *base, int elem, long long row_stride, int n12, int n3,
+                          int planes, long long plane_rows, TmaDesc *out)
+{
+    if (!out || row_stride < kMT || row_stride % 64 || (elem != ELEM_BF16 && elem != ELEM_F16) ||
+        planes < 1 || planes > 2)
+        return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tc_encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const CUtensorMapDataType dt =
+        elem == ELEM_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t row_bytes = (cuuint64_t)row_stride * 2;
+    // components within a 64-component slab, rows of a grid column, grid
+    // columns, slabs, planes
+    const cuuint64_t dims[5] = {64, (cuuint64_t)(n3 + 3), (cuuint64_t)n12,
+                                (cuuint64_t)(row_stride / 64), (cuuint64_t)planes};
+    const cuuint64_t strides[4] = {row_bytes, row_bytes * (cuuint64_t)(n3 + 3), 128,
+                                   row_bytes * (cuuint64_t)plane_rows};
+    const cuuint32_t box[5] = {64, (cuuint32_t)kWin, 4, 2, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap *>(out), dt, 5, const_cast<void *>(base), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t launch_split_pairs(const float *src, long long rows, long long row_stride, int Lreal,
                               unsigned int *bits, float *scales, void *dst, cudaStream_t stream)
 {
@@ -818,8 +954,8 @@ cudaError_t launch_split_pairs(const float *src, long long rows, long long row_s
 }
 
 cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
-                      int ncols, long long plane_rows, const TmaDesc &tmap, int sm_count, int stall,
-                      cudaStream_t stream)
+                      int ncols, long long plane_rows, const TmaDesc &tmap, const TmaDesc *tmap5,
+                      int sm_count, int stall, cudaStream_t stream)
 {
     if (!p.perm || !cell_end || !cols || ncols < 1 || p.n_k || plane_rows >= (1LL << 31))
         return cudaErrorInvalidValue;
@@ -831,11 +967,13 @@ cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const 
     a.mt = (p.Lreal + kMT - 1) / kMT;
     a.plane_rows = (int)plane_rows;
     a.stall = stall;
+    a.wide = tmap5 != nullptr;
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(&tmap);
+    const CUtensorMap &tm5 = *reinterpret_cast<const CUtensorMap *>(tmap5 ? tmap5 : &tmap);
     switch (elem) {
-    case ELEM_F32: return launch_tc_v<__half, 2>(p, a, tm, sm_count, stream);
-    case ELEM_BF16: return launch_tc_v<__nv_bfloat16, 1>(p, a, tm, sm_count, stream);
-    case ELEM_F16: return launch_tc_v<__half, 1>(p, a, tm, sm_count, stream);
+    case ELEM_F32: return launch_tc_v<__half, 2>(p, a, tm, tm5, sm_count, stream);
+    case ELEM_BF16: return launch_tc_v<__nv_bfloat16, 1>(p, a, tm, tm5, sm_count, stream);
+    case ELEM_F16: return launch_tc_v<__half, 1>(p, a, tm, tm5, sm_count, stream);
     default: return cudaErrorInvalidValue;
     }
 }
