@@ -52,6 +52,11 @@ NCU_TRAFFIC = {
     # captured with 128 orbitals, scaled x6 to 768 (rows and outputs grow
     # in proportion to the orbital count)
     ("33f210082c611060", "tio2_batch", "f32", 393216): {(8, 4): 6 * (156558592 + 947191552)},
+    # tensor-core kernel: captured on the electrons of a slab (a_1 < 1/8) of
+    # the batch at the same density (196,327 electrons), scaled by electrons
+    # to the full batch (outputs dominate: traffic grows in proportion)
+    ("45d4e4265bc594a7", "tio2_precision", "f32", 1572864): {
+        (12, 1): (221383168 + 2955751000) * 1572864 // 196327},
 }
 
 # the metric and its unit, identical in every arm of the benchmark
@@ -86,6 +91,9 @@ def parse():
     ap.add_argument("--warm", action="store_true",
                     help="no L2 flush between steps (tables that fit in L2)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--slab", type=float, default=0.0,
+                    help="keep only the electrons with fractional a_1 coordinate below this "
+                         "(a smaller case at the same density, for profiling captures)")
     ap.add_argument("--sweep", default="1,8,32,128,1536",
                     help="batch sizes of the 256-walker sweep extra ('' for none)")
     return ap.parse_args()
@@ -114,6 +122,8 @@ def describe(w, args, E):
          "l2": "warm (no flush between steps)" if args.warm else
                "flushed between steps (512 MB write + 512 MB read, outside the event window)",
          "positions": "uniform in cell" if w.uniform_n else "walker configs + N(0,0.3^2) moves"}
+    if args.slab > 0:
+        d["slab"] = f"electrons with fractional a_1 coordinate below {args.slab} only"
     return d
 
 
@@ -555,6 +565,12 @@ def main():
     spectral = bool(w.extra.get("spectral"))
     tab = w.table(device="cuda") if spectral else w.table()
     pos, offs = w.positions()
+    if args.slab > 0:
+        # the electrons of a slab of the cell (one walker of what is left)
+        u = pos @ np.linalg.inv(np.asarray(w.lattice, dtype=np.float64))
+        pos = np.ascontiguousarray(pos[(u[:, 0] - np.floor(u[:, 0])) < args.slab])
+        offs = np.array([0, len(pos)], dtype=np.int32)
+        args.no_extra = True
     E = len(pos)
     t = pb.BlipTable(w.grid, w.lattice, tab, storage=STORAGE[args.storage])
     if spectral:                       # the FP64 device copy is no longer needed

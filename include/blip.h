@@ -263,7 +263,8 @@ int blip_set_kernel(blip_table t, int variant, int chunks, int warps, int sort);
  * blip_autotune - time each kernel configuration on this batch shape and keep
  * the fastest for batches of this size class (the bit length of n_elec) and
  * output mode (values only, or all five outputs).  Every candidate is timed
- * once; the 12 fastest, median of 7 runs; those within 5 % of the best
+ * once (median of 3 for launches under 0.2 ms); the 16 fastest, median of 7
+ * runs; those within 5 % of the best
  * median, 15 more runs each, interleaved; of these the earliest in the
  * candidate list whose median is within 1 % of the best is kept (a stable
  * choice when the gap is below the timing noise).  Each run follows a read
@@ -349,10 +350,11 @@ int blip_sm_update(int n_walkers, int n, float *dinv, const float *rows, const i
 
 /*
  * blip_test_stall_pipeline - test hook for the failure path (no counterpart
- * in the paper).  With on != 0, launches of the bulk-copy and staged-tile
- * kernels (variants 2 and 8) on this table stall their own pipeline: the consumer warps never release
+ * in the paper).  With on != 0, launches of the bulk-copy, staged-tile and
+ * tensor-core kernels (variants 2, 8 and 12) on this table stall their own
+ * pipeline: the consumers (the tensor-core kernel's MMA thread) never release
  * the first stage, so the producer's bounded wait runs out, it drains the
- * copies it has in flight, and the consumers' bounded waits run out too.
+ * copies it has in flight, and the other roles' bounded waits run out too.
  * The launch returns after a few seconds with BLIP_STATUS_TIMEOUT set and
  * undefined outputs; the context stays usable.  on = 0 restores normal
  * operation.  Nothing faults, traps or spins without a bound.

@@ -839,7 +839,8 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     // scratch, twice the L2, before every run, outside the timed window, so
     // that L2 holds only clean lines), as it runs in a Monte Carlo step
     // between other work.  Three passes: every candidate once (after one
-    // untimed run); the 12 fastest of those, median of 7 runs; the ones
+    // untimed run; median of 3 if under 0.2 ms); the 16 fastest of those,
+    // median of 7 runs; the ones
     // within 5 % of the best median (at most 4), 15 more runs each,
     // interleaved.  The last pass keeps the earliest candidate of the list
     // whose median is within 1 % of the best, so that configurations whose
@@ -865,20 +866,26 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     auto by_time = [](const Timed &a, const Timed &b) {
         return a.first < b.first || (a.first == b.first && a.second < b.second);
     };
-    // first pass: every candidate once
+    // first pass: every candidate once (median of 3 for launches under
+    // 0.2 ms, whose single timings scatter by more than their gaps)
     std::vector<Timed> once;
     for (size_t i = 0; i < cands.size() && rc == 0; ++i) {
         rc = eval_device(t, pos, n_elec, walker_offsets, n_walkers, values, grads, laps, s,
                          cands[i]);
-        float ms = 0.0f;
-        if (rc == 0) rc = timed_run(cands[i], ms);
-        if (rc == 0) once.push_back({ms, i});
+        float ms[3] = {0.0f, 0.0f, 0.0f};
+        if (rc == 0) rc = timed_run(cands[i], ms[0]);
+        if (rc == 0 && ms[0] < 0.2f) {
+            for (int rep = 1; rep < 3 && rc == 0; ++rep) rc = timed_run(cands[i], ms[rep]);
+            std::sort(ms, ms + 3);
+            ms[0] = ms[1];
+        }
+        if (rc == 0) once.push_back({ms[0], i});
     }
-    // second pass: the 12 fastest, median of 7
+    // second pass: the 16 fastest, median of 7
     std::vector<Timed> med;
     if (rc == 0) {
         std::sort(once.begin(), once.end(), by_time);
-        for (size_t j = 0; j < once.size() && j < 12 && rc == 0; ++j) {
+        for (size_t j = 0; j < once.size() && j < 16 && rc == 0; ++j) {
             float ts[7];
             for (int rep = 0; rep < 7 && rc == 0; ++rep) rc = timed_run(cands[once[j].second], ts[rep]);
             if (rc) break;

@@ -9,15 +9,18 @@ kernels, so its bound is derived for its own arithmetic:
   at or above max |a_l|): |v - hi - lo| <= 2^-23 |v|; the FP32 weights
   (about 13 * 2^-24 |W| from their formula) as two FP16 parts,
   |W - hi - lo| <= 2^-22 |W|; the product left out (lo.lo) is below
-  2^-22 |W v|.  Accumulation: 24 products of 16 terms per output (8 K steps
-  x 3 plane pairs); with at most 2 units in the last place of the running
-  sum per product, 24 * 2^-22.  Together about 30 * 2^-22 = 7.1e-6; the
+  2^-22 |W v|.  Accumulation: 24 products of 16 terms per output (16 into
+  the hi-part accumulator: 8 K steps x 2 coefficient planes; 8 into the
+  lo-part one; the two added once); with at most 2 units in the last place
+  of the running sum per product, 24 * 2^-22.  Together about 30 * 2^-22 =
+  7.1e-6; the
   bound takes TAU_TC = 1.6e-5.  Parts below the FP16 normal range (a tiny
   coefficient or weight) are rounded to 2^-25 absolute: a floor of
   2^-25 s_l (sum_s |W_s| + 64) per output.
 * 16-bit tables enter as stored; the weights as two parts of the table's
   type, |W - hi - lo| <= 2^-17 |W| (BF16) or 2^-22 |W| (FP16); 16 products
-  per output.  The same TAU_TC covers this beside the coefficient rounding u
+  per output (8 per part).  The same TAU_TC covers this beside the
+  coefficient rounding u
   of the storage; FP16 has the same subnormal floor with s_l its scale.
 """
 import numpy as np

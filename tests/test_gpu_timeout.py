@@ -1,8 +1,10 @@
-"""The bounded waits of the bulk-copy and staged-tile kernels: a stalled
-pipeline (test hook, the consumers never release the first stage) makes the
-waits run out after about two seconds; the kernel returns, reports BLIP_STATUS_TIMEOUT, and the
-same context evaluates correctly afterwards.  No fault, trap or unbounded
-spin is involved."""
+"""The bounded waits of the bulk-copy, staged-tile and tensor-core kernels: a
+stalled pipeline (test hook: the consumers, or the tensor-core kernel's MMA
+thread, never release the first stage) makes the waits run out after about
+two seconds; the kernel returns, reports BLIP_STATUS_TIMEOUT, and the same
+context evaluates correctly afterwards.  The tensor-core kernel's MMA thread
+waits for its issued products before the tensor memory is freed.  No fault,
+trap or unbounded spin is involved."""
 import time
 
 import numpy as np
@@ -24,7 +26,7 @@ def pb():
     return pb
 
 
-@pytest.mark.parametrize("cfg", [(2, 1, 2, 0), (8, 4, 16, 1)])
+@pytest.mark.parametrize("cfg", [(2, 1, 2, 0), (8, 4, 16, 1), (12, 1, 1, 1)])
 def test_stalled_pipeline_times_out_and_context_survives(pb, cfg):
     grid = (8, 8, 8)
     lat = pins.triclinic_lattice()
@@ -32,7 +34,7 @@ def test_stalled_pipeline_times_out_and_context_survives(pb, cfg):
     tab = bi.smooth_random_table(grid, 512, seed=61)
     pos = np.random.default_rng(61).uniform(0, 1, size=(64, 3)) @ lat
     t = pb.BlipTable(grid, lat, tab)
-    t.set_kernel(*cfg)                       # bulk copy with 2 stages, or staged tiles
+    t.set_kernel(*cfg)                       # bulk copy with 2 stages, staged tiles, tensor cores
     t.status()
     pb.lib().blip_test_stall_pipeline(t.handle, 1)
     t0 = time.time()

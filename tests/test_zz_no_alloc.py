@@ -120,7 +120,7 @@ def test_noalloc_with_the_staged_tile_kernel(pb):
 
 @pytest.mark.parametrize("cfg", [(11, 1, 8, 1), (11, 1, 8, 2), (10, 1, 4, 1), (5, 2, 4, 1),
                                  (5, 4, 8, 1), (2, 2, 8, 1), (9, 1, 8, 2), (3, 2, 4, 2),
-                                 (6, 1, 8, 1), (7, 1, 8, 1)])
+                                 (6, 1, 8, 1), (7, 1, 8, 1), (12, 1, 1, 1)])
 def test_noalloc_with_each_sorted_kernel(pb, cfg):
     """Every kernel the entry point can run on the sorted order - without the
     per-electron geometry records blip_eval's sort makes, so each kernel
