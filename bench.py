@@ -697,6 +697,8 @@ def main():
     if not args.no_extra and rank == 0 and tab is not None and w.name in ("tio2_precision",
                                                                            "tio2"):
         extras_single_walker(args, pb, w, tab, t, st_, line, sms, stream)
+    if not args.no_extra and rank == 0 and w.name == "tio2_precision":
+        extras_l2(args, pb, line, sms)
 
     if w.is_complex:
         line["real_equivalent_value"] = 2 * value
@@ -778,14 +780,17 @@ def extras_precision(args, pb, w, tab, pos, dpos, doffs, t32, out, st_, line, sm
     ra = {}
     for storage in ("f32", "bf16"):
         t = tables[storage]
-        best = None
-        for srt in (0, 1):
-            ms_l = st_.time(lambda: t.eval_ratio(dpos, cols, doffs, sort=srt), max(3, K // 4))
-            ent = _timed_entry(ms_l, E, Lr, U, ELEM_BYTES[storage], "ratio", sms)
-            ent["sort"] = srt
-            if best is None or ent["us"] < best["us"]:
-                best = ent
-        ra[storage] = best
+        # sort 1: cell order, the tensor cores for this dense batch; sort 2:
+        # cell order on the CUDA cores
+        ms_l = st_.time(lambda: t.eval_ratio(dpos, cols, doffs, sort=1), max(3, K // 2))
+        ent = _timed_entry(ms_l, E, Lr, U, ELEM_BYTES[storage], "ratio", sms, (12, 1, 1, 1),
+                           storage)
+        ent["sort"] = 1
+        ms_c = st_.time(lambda: t.eval_ratio(dpos, cols, doffs, sort=2), max(3, K // 4))
+        core = _timed_entry(ms_c, E, Lr, U, ELEM_BYTES[storage], "ratio", sms)
+        ent["cuda_cores_sorted"] = {k: core[k] for k in ("us", "evals_per_s", "bound", "frac")}
+        ent["status"] = t.status()
+        ra[storage] = ent
     line["ratio"] = ra
 
     # 256 walkers x b electrons per walker per launch, FP32 and BF16
@@ -805,6 +810,61 @@ def extras_precision(args, pb, w, tab, pos, dpos, doffs, t32, out, st_, line, sm
             ent.update({"b": b, "E": Eb, "storage": storage})
             sweep.append(ent)
     line["batch_sweep"] = sweep
+
+
+def extras_l2(args, pb, line, sms):
+    """A table that fits in L2: the TiO2 primitive cell with 64 k-points
+    (15 MB complex64) for 256 walkers x 128 moves drawn in the 4 x 4 x 4
+    supercell, on a stream of its own: warm (nothing between launches), and
+    with an L2 flush between launches (standing in for the rest of a Monte
+    Carlo step) without and with the table's L2 access-policy window; beside
+    the L2 read bandwidth of blip_probe_l2_read on a 48 MB buffer."""
+    import torch
+    w = bi.workload("tio2_kpoints")
+    tab = w.table()
+    pos, offs = w.positions()
+    E = len(pos)
+    t = pb.BlipTable(w.grid, w.lattice, tab, storage=STORAGE["c64"])
+    t.set_kpoints(w.extra["kfrac"], w.extra["koffs"])
+    s = torch.cuda.Stream()
+    warm, cold = Stepper(True, s), Stepper(False, s)
+    K = args.steps
+    Lr = t.info()["Lreal"]
+    res = {"workload": "tio2_kpoints: primitive cell 4.35 x 4.35 x 2.8 bohr, grid 18x18x12, "
+                       "64 k-points x 6 complex orbitals (15 MB complex64), "
+                       f"{E} electrons (256 walkers x 128 moves in the supercell)",
+           "table_bytes": t.info()["table_bytes"]}
+    with torch.cuda.stream(s):
+        dpos = torch.from_numpy(pos).cuda()
+        doffs = torch.from_numpy(offs).cuda()
+        out = t.alloc_outputs(E)
+        ch = t.autotune(dpos, doffs, out=out, stream=s)
+        ev = lambda: t.eval(dpos, doffs, out=out, stream=s)
+        times = {"warm": statistics.mean(warm.time(ev, K)),
+                 "flushed_window_off": statistics.mean(cold.time(ev, K))}
+        t.set_l2_residency(1.0)
+        times["flushed_window_on"] = statistics.mean(cold.time(ev, K))
+        t.set_l2_residency(0.0)
+        buf = torch.ones(12 * 1024 * 1024, device="cuda")           # 48 MB
+        reps = 50
+        pms = statistics.mean(warm.time(lambda: pb.probe_l2_read(buf, reps, stream=s), 5))
+    s.synchronize()
+    l2_gbs = buf.numel() * 4 * reps / (pms / 1e3) / 1e9
+    gather = 64.0 * Lr * 4 * E                  # stencil rows, served by L2 when resident
+    outb = 20.0 * Lr * E
+    peak, _ = measured_peaks()
+    f32_peak = sms * 128 * 2 * 2.07e9 / 1e12
+    roof = {"l2": gather / (l2_gbs * 1e9), "hbm": outb / (peak * 1e9),
+            "alu": 640.0 * Lr * E / (f32_peak * 1e12)}
+    bound = max(roof, key=roof.get)
+    for name, ms in times.items():
+        res[name] = {"us": 1e3 * ms, "evals_per_s": E * w.n_orb / (ms / 1e3),
+                     "l2_GBps": gather / (ms / 1e3) / 1e9, "bound": bound,
+                     "frac": roof[bound] / (ms / 1e3)}
+    res.update({"kernel": list(ch), "l2_read_probe_GBps": l2_gbs,
+                "roof_us": {k: 1e6 * v for k, v in roof.items()}})
+    line["l2_resident"] = res
+    t.close()
 
 
 def extras_single_walker(args, pb, w, tab, t, st_, line, sms, stream):

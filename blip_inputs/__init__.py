@@ -279,17 +279,19 @@ class Workload:
     ragged: tuple = None        # (lo, hi) for ragged batch sizes
     uniform_n: int = 0          # >0: plain uniform positions (single walker)
     extra: dict = field(default_factory=dict)
+    pos_lattice: np.ndarray = None   # cell the positions are drawn in (None: lattice)
 
     def positions(self):
         """(positions [E][3] float64, offsets [W+1] int32)."""
+        cell = self.lattice if self.pos_lattice is None else self.pos_lattice
         if self.uniform_n:
-            p = uniform_positions(self.lattice, self.uniform_n, self.pos_seed)
+            p = uniform_positions(cell, self.uniform_n, self.pos_seed)
             return p, np.array([0, self.uniform_n], dtype=np.int32)
         if self.ragged is not None:
             b = ragged_batch_sizes(self.n_walkers, self.ragged[0], self.ragged[1], self.pos_seed)
         else:
             b = self.batch
-        return walker_positions(self.lattice, self.n_walkers, self.n_per_walker, b, self.pos_seed)
+        return walker_positions(cell, self.n_walkers, self.n_per_walker, b, self.pos_seed)
 
     def table(self, dtype=None, threads=None, device="cpu", orbitals=None):
         """The coefficient table.  Complex supercell workloads use the
@@ -321,6 +323,12 @@ def workload(name: str, **kw) -> Workload:
     * ``tio2_batch``: the same table, 256 walkers, ``batch`` moved electrons
       per walker (keyword ``batch``, default 1536).
     * ``tio2_precision``: the same table, 1,024 walkers x 1,536 electrons.
+    * ``tio2_kpoints``: the primitive cell of the TiO2 cell (4.35 x 4.35 x 2.8
+      bohr, a quarter along each axis), 18 x 18 x 12 grid, 64 k-points (the
+      4 x 4 x 4 mesh kappa in {0, 1/4, 1/2, 3/4}^3) x 6 complex orbitals =
+      384 complex orbitals (a 15 MB complex64 table), positions of 256
+      walkers x ``batch`` moves drawn in the 4 x 4 x 4 supercell (the TiO2
+      cell); ``extra`` holds kfrac [64][3] and koffs [65].
     * ``tio2_super_complex``: 2 x 2 x 2 supercell (34.8 x 34.8 x 22.4 bohr),
       144 x 144 x 96 grid, 1,536 complex orbitals (Fourier-space table
       recipe), 512 walkers with batch sizes uniform in {1..512}.
@@ -342,6 +350,18 @@ def workload(name: str, **kw) -> Workload:
         w = Workload(name, TIO2_CELL, TIO2_GRID, kw.pop("n_orb", 768), table_seed=0,
                      pos_seed=103, n_walkers=kw.pop("n_walkers", 1024), n_per_walker=1536,
                      batch=1536)
+    elif name == "tio2_kpoints":
+        nk_axis = 4
+        ks = [(i / nk_axis, j / nk_axis, k / nk_axis) for i in range(nk_axis)
+              for j in range(nk_axis) for k in range(nk_axis)]
+        per_k = kw.pop("per_k", 6)
+        w = Workload(name, tetragonal_lattice(17.4 / 4, 11.2 / 4), (18, 18, 12), per_k * len(ks),
+                     is_complex=True, table_seed=0, pos_seed=105,
+                     n_walkers=kw.pop("n_walkers", 256), n_per_walker=1536,
+                     batch=kw.pop("batch", 128),
+                     extra={"kfrac": np.array(ks, dtype=np.float64),
+                            "koffs": np.arange(0, per_k * len(ks) + 1, per_k, dtype=np.int32)},
+                     pos_lattice=TIO2_CELL)
     elif name == "tio2_super_complex":
         w = Workload(name, tetragonal_lattice(34.8, 22.4), (144, 144, 96), kw.pop("n_orb", 1536),
                      is_complex=True, table_seed=0, pos_seed=104,

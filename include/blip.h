@@ -41,6 +41,8 @@
 #ifndef BLIP_H
 #define BLIP_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -288,7 +290,7 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
  * |k|^2 u).  This lets a primitive-cell table with n_k k-points stand in for
  * a supercell table n_k times larger (the paper's TiO2 orbitals are complex,
  * Sec. VI.A; the phase convention is not stated there).
- *   n_k      0 (clear) .. 16
+ *   n_k      0 (clear) .. 64
  *   kfrac    host [n_k][3] kappa_q in reciprocal-lattice units
  *   koffs    host [n_k + 1] complex-orbital offsets, 0 = koffs[0] <= ... <=
  *            koffs[n_k] = n_orb
@@ -316,7 +318,12 @@ int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koff
  *              d/dz psi, lap psi}_l(r'_j) inv_cols[j][l]
  *   values     device [n_elec][n_orb] float for the new rows psi_l(r'_j)
  *              (needed to update D^{-1} after an accepted move), or NULL
- *   sort       0: input order; 1: evaluate in grid-cell order (same results)
+ *   sort       0: input order; 1: grid-cell order, and for dense batches
+ *              (n_elec >= half the grid cells) the tensor-core kernel
+ *              (matrix products over the union rows of up to 25 electrons,
+ *              FP32 accumulation; its rounding differs from the CUDA cores'
+ *              within the per-output bound 1.6e-5 sum_s |W_o(s)| |a_ls|);
+ *              2: grid-cell order on the CUDA cores only
  * Other arguments as blip_eval.  Deterministic (fixed reduction order).
  * Errors: INVALID_ARG, UNSUPPORTED_DTYPE (complex tables), CUDA.
  */
@@ -360,6 +367,37 @@ int blip_sm_update(int n_walkers, int n, float *dinv, const float *rows, const i
  * operation.  Nothing faults, traps or spins without a bound.
  */
 int blip_test_stall_pipeline(blip_table t, int on);
+
+/*
+ * blip_set_l2_residency - keep (a share of) the table resident in L2 across
+ * evaluations.  For tables that fit in the persisting part of L2 - a
+ * primitive-cell table with k-points (blip_set_kpoints) instead of a
+ * supercell table, Sec. VI.C's cache trials - the coefficient rows of every
+ * launch are then L2 hits even though the outputs stream through L2.
+ *   fraction   0: off; (0, 1]: the share of the table's bytes in the window
+ * The window is capped by the device's largest access-policy window, the
+ * persisting part by its persisting-L2 maximum (a window larger than that is
+ * marked persisting in proportion, the hit ratio).  This sets the context's
+ * persisting-L2 limit (cudaLimitPersistingL2CacheSize), a per-context setting
+ * that ends with the context; turning the window off or destroying the table
+ * resets it to 0 and returns the persisting lines to normal.  Evaluation
+ * launches on a stream created by the caller carry the window (the stream's
+ * own window is restored after each launch); launches on the legacy default
+ * stream (NULL) run without it.  Outputs are unchanged.  Errors:
+ * INVALID_ARG (fraction outside [0, 1], another device current, no
+ * persisting L2 on the device), CUDA.
+ */
+int blip_set_l2_residency(blip_table t, double fraction);
+
+/*
+ * blip_probe_l2_read - a measurement aid, not an evaluation: read the device
+ * buffer buf (bytes, a multiple of 16, 16-byte aligned) reps times in one
+ * launch, every load through L2 with L1 bypassed.  Timed on a buffer that
+ * fits in L2 it gives the L2 -> SM read bandwidth that bounds evaluations of
+ * L2-resident tables.  Asynchronous on stream; nothing is written.  Errors:
+ * INVALID_ARG, CUDA.
+ */
+int blip_probe_l2_read(const void *buf, size_t bytes, int reps, void *stream);
 
 /*
  * blip_test_fail_alloc - test hook for the out-of-memory path (no

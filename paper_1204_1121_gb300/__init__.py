@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["lib", "BlipTable", "BlipError", "sm_update", "F32", "BF16", "F16", "C64", "BF16PAIR",
+__all__ = ["lib", "BlipTable", "BlipError", "sm_update", "probe_l2_read", "F32", "BF16", "F16", "C64", "BF16PAIR",
            "NORM_BSPLINE", "NORM_ALFE_GILLAN", "STATUS_NONFINITE_POS", "STATUS_FAR_POS",
            "STATUS_BAD_OFFSETS", "STATUS_TIMEOUT", "STATUS_LAYOUT", "EXPORTED"]
 
@@ -50,6 +50,8 @@ EXPORTED = {
     "blip_sm_update": (I, [I, I, P, P, P, P, P]),
     "blip_test_stall_pipeline": (I, [P, I]),
     "blip_test_fail_alloc": (I, [I]),
+    "blip_set_l2_residency": (I, [P, ctypes.c_double]),
+    "blip_probe_l2_read": (I, [P, ctypes.c_size_t, I, P]),
     "blip_probe_gather": (I, [P, P, I, P, P, P, I, P]),
 }
 
@@ -291,6 +293,11 @@ class BlipTable:
         _check(self._lib.blip_set_kpoints(self._h, kf.shape[0], P(kf.ctypes.data),
                                           P(ko.ctypes.data)), "blip_set_kpoints")
 
+    def set_l2_residency(self, fraction):
+        """Keep a share of the table resident in L2 (``blip_set_l2_residency``);
+        0 turns it off.  Applies to launches on non-default streams."""
+        _check(self._lib.blip_set_l2_residency(self._h, float(fraction)), "blip_set_l2_residency")
+
     def set_kernel(self, variant=1, chunks=1, warps=8, sort=0):
         _check(self._lib.blip_set_kernel(self._h, variant, chunks, warps, sort), "blip_set_kernel")
 
@@ -326,6 +333,15 @@ class BlipTable:
         if isinstance(x, torch.Tensor):
             return torch.view_as_complex(x.reshape(*x.shape[:-1], -1, 2))
         return x.view(np.complex64)
+
+
+def probe_l2_read(buf, reps, stream=None):
+    """Measurement aid (``blip_probe_l2_read``): read the CUDA tensor ``buf``
+    ``reps`` times through L2 in one launch."""
+    if not (buf.is_cuda and buf.is_contiguous()):
+        raise TypeError("buf must be a contiguous CUDA tensor")
+    _check(lib().blip_probe_l2_read(P(buf.data_ptr()), buf.numel() * buf.element_size(),
+                                    int(reps), _stream_ptr(stream)), "blip_probe_l2_read")
 
 
 def sm_update(dinv, rows, cols, work=None, stream=None):

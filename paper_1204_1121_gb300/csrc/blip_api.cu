@@ -69,6 +69,11 @@ struct blip_table_s {
     TmaDesc tc_tmap5 = {};
     bool tc_wide = false;
     bool tc_ready = false;
+    // L2 residency: access-policy window over the table (bytes, 0 = off) and
+    // whether this table set the context's persisting-L2 limit
+    size_t l2_window = 0;
+    float l2_hit_ratio = 1.0f;
+    bool l2_limit_set = false;
     // Bloch k-points (complex tables)
     int n_k = 0;
     int koff[kMaxKpoints + 1] = {};
@@ -347,12 +352,44 @@ EvalParams make_params(const blip_table_s *t, const double *pos, int n_elec, con
     return p;
 }
 
+// While alive, launches on stream carry the table's L2 access-policy window
+// (hits persist, misses stream); the stream's previous window comes back
+// afterwards.  Streams that take no window (the legacy default stream) are
+// launched without it.
+struct L2Window {
+    cudaStream_t s = nullptr;
+    cudaStreamAttrValue old{};
+    bool set = false;
+    L2Window(const blip_table_s *t, cudaStream_t stream) : s(stream)
+    {
+        if (!t->l2_window || !stream) return;
+        if (cudaStreamGetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &old) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        cudaStreamAttrValue v{};
+        v.accessPolicyWindow.base_ptr = t->d_table;
+        v.accessPolicyWindow.num_bytes = t->l2_window;
+        v.accessPolicyWindow.hitRatio = t->l2_hit_ratio;
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        set = cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &v) == cudaSuccess;
+        if (!set) cudaGetLastError();
+    }
+    ~L2Window()
+    {
+        if (set && cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &old) != cudaSuccess)
+            cudaGetLastError();
+    }
+};
+
 // Launch kernel choice kc on prepared parameters; scratch holds the sort
 // whose views the grouped and staged kernels read.
 int launch_choice(blip_table_s *t, const EvalParams &p, const KernelChoice &kc, void *scratch,
                   cudaStream_t stream)
 {
     if (t->n_k && !has_bloch_epilogue(kc)) return BLIP_ERR_INVALID_ARG;
+    const L2Window window(t, stream);
     if (kc.variant == VAR_BULK) {
         const size_t smem = bulk_smem_bytes(kc.chunks, kc.warps);
         int per_sm = (int)((228 * 1024) / (smem + 1024));
@@ -433,6 +470,10 @@ void free_table(blip_table_s *t)
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != t->device) cudaSetDevice(t->device);
+    if (t->l2_limit_set) {
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
+    }
     if (t->d_table) cudaFree(t->d_table);
     if (t->d_scales) cudaFree(t->d_scales);
     if (t->d_status) cudaFree(t->d_status);
@@ -941,6 +982,48 @@ int blip_autotune(blip_table t, const double *pos, int n_elec, const int *walker
     return BLIP_OK;
 }
 
+int blip_set_l2_residency(blip_table t, double fraction)
+{
+    if (!t || !(fraction >= 0.0) || fraction > 1.0) return BLIP_ERR_INVALID_ARG;
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != t->device) return BLIP_ERR_INVALID_ARG;
+    if (fraction == 0.0) {
+        if (t->l2_limit_set) {
+            if (t->used) CK(cudaStreamSynchronize(t->last_stream));
+            CK(cudaCtxResetPersistingL2Cache());
+            CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0));
+            t->l2_limit_set = false;
+        }
+        t->l2_window = 0;
+        return BLIP_OK;
+    }
+    int max_persist = 0, max_window = 0;
+    CK(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev));
+    CK(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev));
+    if (max_persist <= 0 || max_window <= 0) return BLIP_ERR_INVALID_ARG;
+    const size_t want = (size_t)(fraction * (double)t->table_bytes);
+    const size_t window = std::min(want, (size_t)max_window);
+    const size_t limit = std::min(window, (size_t)max_persist);
+    CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit));
+    t->l2_limit_set = true;
+    t->l2_window = window;
+    // more window than persisting lines: mark only a share of it persisting
+    t->l2_hit_ratio = window > 0 ? std::min(1.0f, (float)((double)limit / (double)window)) : 1.0f;
+    return BLIP_OK;
+}
+
+int blip_probe_l2_read(const void *buf, size_t bytes, int reps, void *stream)
+{
+    if (!buf || bytes < 16 || bytes % 16 || ((uintptr_t)buf & 15u) || reps < 1)
+        return BLIP_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(launch_l2_read(buf, bytes, reps, sms, static_cast<cudaStream_t>(stream)));
+    return BLIP_OK;
+}
+
 int blip_test_fail_alloc(int n)
 {
     g_alloc_fail_after.store(n < 0 ? -1 : n);
@@ -1004,7 +1087,7 @@ int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walk
     if (!t || n_elec < 0 || (walker_offsets && n_walkers < 1)) return BLIP_ERR_INVALID_ARG;
     if (n_elec > 0 && (!pos || !inv_cols || !ratio)) return BLIP_ERR_INVALID_ARG;
     if (t->is_complex) return BLIP_ERR_UNSUPPORTED_DTYPE;
-    if (sort != 0 && sort != 1) return BLIP_ERR_INVALID_ARG;
+    if (sort < 0 || sort > 2) return BLIP_ERR_INVALID_ARG;
     if (n_elec == 0) return BLIP_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EvalParams p{};
@@ -1034,7 +1117,29 @@ int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walk
     p.laps = nullptr;
     p.vec_out = 0;
     p.status = t->d_status;
-    CK(launch_ratio(p, t->elem, inv_cols, ratio, 4, s));
+    // dense batches (at least one electron per two cells) in cell order go
+    // to the tensor cores; the operand planes and tensor maps are made on
+    // first use, outside stream capture
+    bool tc = false;
+    if (sort == 1 && 2LL * n_elec >= (long long)t->grid[0] * t->grid[1] * t->grid[2]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(s, &cs));
+        if (t->tc_ready || cs == cudaStreamCaptureStatusNone) {
+            const int rc = tc_prepare(t);
+            if (rc != BLIP_OK && rc != BLIP_ERR_INVALID_ARG) return rc;
+            tc = rc == BLIP_OK;
+        }
+    }
+    if (tc) {
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
+        if (t->elem == ELEM_F32) p.scales = t->d_tc_scales;   // the planes' power-of-two scales
+        CK(launch_tc(p, t->elem, cell_end, t->d_cols, t->ncols, t->rows, t->tc_tmap,
+                     t->tc_wide ? &t->tc_tmap5 : nullptr, t->sm_count, t->test_stall, s, inv_cols,
+                     ratio));
+    } else {
+        CK(launch_ratio(p, t->elem, inv_cols, ratio, 4, s));
+    }
     t->last_stream = s;
     t->used = true;
     return BLIP_OK;

@@ -273,12 +273,12 @@ __device__ __forceinline__ int stencil_geometry_warp(const EvalParams &p, int e,
         // reduction of kappa . u mod 1, then an FP32 sin/cos of 2 pi x)
         const double u0 = __shfl_sync(FULL, ua, 0), u1 = __shfl_sync(FULL, ua, 1),
                      u2 = __shfl_sync(FULL, ua, 2);
-        if (lane < p.n_k && !(bad & BLIP_STATUS_NONFINITE_POS)) {
-            const double *kf = p.kfrac[lane];
+        for (int q = lane; q < p.n_k && !(bad & BLIP_STATUS_NONFINITE_POS); q += 32) {
+            const double *kf = p.kfrac[q];
             const double x = fma(kf[0], u0, fma(kf[1], u1, kf[2] * u2));
             float sn, cs;
             sincospif(2.0f * (float)(x - floor(x)), &sn, &cs);
-            ws.phase[lane] = make_float2(cs, sn);
+            ws.phase[q] = make_float2(cs, sn);
         }
     }
     const int i0 = __shfl_sync(FULL, ia, 0), i1 = __shfl_sync(FULL, ia, 1),
@@ -329,9 +329,14 @@ __device__ __forceinline__ void apply_bloch(const EvalParams &p, int l0, const f
 {
 #pragma unroll
     for (int v = 0; v < VEC; v += 2) {
+        // the k-point of complex orbital lc: the last q with koff[q] <= lc
         const int lc = (l0 + v) >> 1;
-        int q = 0;
-        for (int j = 1; j < p.n_k; ++j) q += lc >= p.koff[j] ? 1 : 0;
+        int q = 0, hi = p.n_k;
+        while (hi - q > 1) {
+            const int mid = (q + hi) >> 1;
+            if (p.koff[mid] <= lc) q = mid;
+            else hi = mid;
+        }
         const float2 ph = phase[q];
         const float ur = acc[0][v], ui = acc[0][v + 1];
         acc[0][v] = ph.x * ur - ph.y * ui;

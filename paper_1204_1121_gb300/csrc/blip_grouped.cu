@@ -127,11 +127,33 @@ __global__ void __launch_bounds__(256) blip_eval_grouped(EvalParams p, const int
     }
 }
 
+// Raise one instantiation's dynamic shared-memory cap once (8 warps x 4
+// slices pass the 48 KB default).
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t smem, bool &done)
+{
+    if (done || smem <= 48 * 1024) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 template <typename T, int G, bool VONLY>
 cudaError_t launch_grouped_t(const EvalParams &p, int warps, const int *keys, const int *cell_end,
                              cudaStream_t stream)
 {
     const size_t smem = sizeof(WarpSlice) * (size_t)warps * G;
+    static bool done[3] = {false, false, false};
+    cudaError_t e = cudaSuccess;
+    if (p.n_k) {
+        if constexpr (!std::is_same<T, __half>::value)
+            e = allow_smem(blip_eval_grouped<T, G, VONLY, 1>, smem, done[1]);
+    } else if (p.georec) {
+        e = allow_smem(blip_eval_grouped<T, G, VONLY, 2>, smem, done[2]);
+    } else {
+        e = allow_smem(blip_eval_grouped<T, G, VONLY, 0>, smem, done[0]);
+    }
+    if (e != cudaSuccess) return e;
     long long blocks = (p.items + warps - 1) / warps;
     if (blocks < 1) blocks = 1;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;

@@ -32,7 +32,7 @@ enum Variant {
                               // column: tensor-core products over their union rows
 };
 
-constexpr int kMaxKpoints = 16;
+constexpr int kMaxKpoints = 64;   // a 4 x 4 x 4 k-point mesh
 
 // Cell geometry, prepared once on the host in FP64.
 struct Geometry {
@@ -191,19 +191,22 @@ cudaError_t make_tc_tmap(const void *base, int elem, long long row_stride, long 
 // row_stride words.
 cudaError_t launch_split_pairs(const float *src, long long rows, long long row_stride, int Lreal,
                               unsigned int *bits, float *scales, void *dst, cudaStream_t stream);
-// Launch the tensor-core kernel (needs the sort): elem = ELEM_BF16 / ELEM_F16
-// (tmap over the table, p.scales its per-component scales or null) or ELEM_F32
-// (tmap over its two FP16 planes, each plane_rows rows, p.scales their
-// power-of-two scales); tmap5: the 5-D view (or null: 1 KB boxes only);
-// cols: the ncols column keys in sort order.
 // The 5-D view of the same operand for 8 KB boxes: components within a
 // 64-component slab, rows of a grid column (n3 + 3), grid columns (n1 n2),
 // slabs, planes; box 64 x 8 x 4 x 2 x 1.
 cudaError_t make_tc_tmap5(const void *base, int elem, long long row_stride, int n12, int n3,
                           int planes, long long plane_rows, TmaDesc *out);
+// Launch the tensor-core kernel (needs the sort): elem = ELEM_BF16 / ELEM_F16
+// (tmap over the table, p.scales its per-component scales or null) or ELEM_F32
+// (tmap over its two FP16 planes, each plane_rows rows, p.scales their
+// power-of-two scales); tmap5: the 5-D view (or null: 1 KB boxes only);
+// cols: the ncols column keys in sort order.  Ratio mode when ratio is not
+// null: rcols [n_elec][Lreal] the inverse columns, ratio [n_elec][5] the
+// contraction, p.values the new rows or null, p.grads and p.laps null.
 cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
                       int ncols, long long plane_rows, const TmaDesc &tmap, const TmaDesc *tmap5,
-                      int sm_count, int stall, cudaStream_t stream);
+                      int sm_count, int stall, cudaStream_t stream, const float *rcols = nullptr,
+                      float *ratio = nullptr);
 
 // Launch the split-stencil kernel: a block of 4 warps per (electron, chunk),
 // warp q contracting the 16 sites of a_1 slab q, partial sums added in a
@@ -218,6 +221,9 @@ cudaError_t launch_sm_update(int n_walkers, int n, float *dinv, const float *row
 // Read bytes of buf through L2 (no writes): afterwards L2 holds clean lines
 // of buf only (the autotuner's cold start).
 cudaError_t launch_l2_sweep(const void *buf, size_t bytes, int sm_count, cudaStream_t stream);
+// Read bytes of buf reps times through L2, L1 bypassed (a measurement aid).
+cudaError_t launch_l2_read(const void *buf, size_t bytes, int reps, int sm_count,
+                           cudaStream_t stream);
 
 // Table construction kernels (blip_table.cu).
 // Convert rows [row0, row0 + nrows) of a source table [n1*n2*n3][Lreal]

@@ -42,6 +42,14 @@
 //               per-slot records, or the FP64 wrap), their 64 x 5 weights
 //               split into 16-bit planes, written as B operand core
 //               matrices into one of two buffers.
+// Ratio mode (blip_eval_ratio): the epilogue contracts the accumulator
+// columns with the inverse Slater column of each electron instead of storing
+// them, sum_l D^T[l][(j, o)] c_j[l] (the quasi-simultaneous ratio and its
+// derivatives): per lane over the M tiles of a part, then over the 32 lanes
+// (a fixed butterfly that leaves each lane two column totals), then over the
+// four lane quarters in shared memory (the part's weight buffer, free once
+// its last product is done), in a fixed order; five numbers per electron
+// leave the chip (plus the new orbital row if asked for).
 // Every wait is bounded (about 2 s of global time): a wait that runs out
 // sets BLIP_STATUS_TIMEOUT and an abort flag; every role then winds down,
 // the producer waits (bounded) for its copies in flight and the MMA thread
@@ -103,6 +111,7 @@ struct __align__(16) PartInfo {
     int n;              // MMA N: outputs x cnt rounded up to 16
     int pad[2];
     float *dst[kNmax];  // output row of accumulator column NO j + o (electron j, output o)
+    int eid[32];        // ratio mode: electron index of part electron j
 };
 
 struct TcArgs {
@@ -114,6 +123,8 @@ struct TcArgs {
     int plane_rows;        // rows of one coefficient plane in the tensor map
     int stall;             // test hook: the MMA thread never releases the first stage
     int wide;              // 1: the 5-D tensor map (8 KB boxes) is usable
+    const float *rcols;    // ratio mode: [n_elec][Lreal] inverse columns, else null
+    float *ratio;          // ratio mode: [n_elec][5] output, else null
 };
 
 template <int APL, bool VONLY>
@@ -322,17 +333,150 @@ template <> __device__ __forceinline__ float from_bits<__half>(unsigned short b)
     return __half2float(__ushort_as_half(b));
 }
 
+// 8 consecutive accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Epilogue of the ratio mode for one warp: lane quarter q of the
+// accumulator, the 32-column chunks c0 = 32 HALF + 64 i (i = 0, 1) of the
+// part's 5 cnt columns (electron j = column / 5, output o = column % 5).
+// Per M tile each lane folds its orbital component l into 64 running sums,
+// sum over tiles of (hi + lo weight part columns) s_l c_j[l]; at the
+// end of the part a butterfly over the lanes leaves lane L the totals of its
+// chunk columns 2 L and 2 L + 1, the four quarters meet in the part's weight
+// buffer, and thread et < 5 cnt of the epilogue writes
+// ratio[e_j][o] = q0 + q1 + q2 + q3 (this order).  Returns false on abort.
+template <int HALF, int RLO, int ACC_COLS, int NACC>
+__device__ __forceinline__ bool ratio_epilogue(const EvalParams &p, const TcArgs &a,
+                                               PartInfo *info, unsigned char *wbuf,
+                                               uint32_t w_buf_bytes, uint64_t *w_full,
+                                               uint64_t *acc_full, uint64_t *acc_empty,
+                                               uint64_t *epi_done, uint64_t *red_done,
+                                               uint32_t tmem, int q, int lane, int et,
+                                               volatile int *abort_flag)
+{
+    const size_t L = (size_t)p.Lreal;
+    int tile = 0;
+    for (int part = 0;; ++part) {
+        const int wi = (int)(part & 1);
+        const unsigned ph = (unsigned)((part >> 1) & 1);
+        if (!wait_bar(w_full + wi, ph, abort_flag)) {
+            if (lane == 0) raise_abort(p, abort_flag);
+            return false;
+        }
+        const int cnt = info[wi].cnt;
+        if (cnt < 0) return true;
+        const int ncol = 5 * cnt;
+        const int *eid = info[wi].eid;
+        float acc[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) acc[i] = 0.0f;
+        for (int m = 0; m < a.mt; ++m) {
+            const int ab = (int)(tile % NACC);
+            const int l = m * kMT + 32 * q + lane;
+            const bool in = l < p.Lreal;
+            const float sc = (p.scales && in) ? p.scales[l] : 1.0f;
+            // s_l c_j[l] of the chunks' electrons, loaded ahead of the
+            // accumulator (each inverse entry is read once: streaming loads)
+            float cv[2][8];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int c0 = 32 * HALF + 64 * i;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = c0 / 5 + u;
+                    cv[i][u] = (in && j <= (c0 + 31) / 5 && j < cnt)
+                                   ? __ldcs(a.rcols + (size_t)eid[j] * L + l) * sc
+                                   : 0.0f;
+                }
+            }
+            if (!wait_bar(acc_full + ab, (unsigned)((tile / NACC) & 1), abort_flag)) {
+                if (lane == 0) raise_abort(p, abort_flag);
+                return false;
+            }
+            tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * ACC_COLS);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int c0 = 32 * HALF + 64 * i;
+                if (c0 >= ncol) break;                   // the same for the whole warp
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {            // 8 columns at a time
+                    uint32_t r[8], rl[8];
+                    tmem_ld8_nowait(taddr + c0 + 8 * g, r);              // hi weight part
+                    tmem_ld8_nowait(taddr + RLO + c0 + 8 * g, rl);       // lo weight part
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int cc = c0 + 8 * g + jj, u = cc / 5 - c0 / 5;
+                        if (cc < ncol) {
+                            const float v = __uint_as_float(r[jj]) + __uint_as_float(rl[jj]);
+                            acc[32 * i + 8 * g + jj] = fmaf(v, cv[i][u], acc[32 * i + 8 * g + jj]);
+                            if (cc % 5 == 0 && p.values && in)
+                                __stcs(p.values + (size_t)eid[cc / 5] * L + l, v * sc);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + ab);
+            ++tile;
+        }
+        // over the lanes: after the step with offset o the lanes with bit o
+        // set keep the upper half of the sums in play
+#pragma unroll
+        for (int st = 0; st < 5; ++st) {
+            const int o = 16 >> st, h = 32 >> st;
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const float send = up ? acc[i] : acc[i + h];
+                const float keep = up ? acc[i + h] : acc[i];
+                acc[i] = keep + __shfl_xor_sync(FULL, send, o);
+            }
+        }
+        // the part's weight buffer is free: its last product has completed
+        float *scr = reinterpret_cast<float *>(wbuf + (uint32_t)wi * w_buf_bytes);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int k = 2 * lane + t;
+            scr[q * 128 + 32 * HALF + 64 * (k >> 5) + (k & 31)] = acc[t];
+        }
+        mbar_arrive(red_done + wi);                      // all 32 kEpiWarps threads
+        if (!wait_bar(red_done + wi, ph, abort_flag)) {
+            if (lane == 0) raise_abort(p, abort_flag);
+            return false;
+        }
+        if (et < ncol) {
+            const float tot = ((scr[et] + scr[128 + et]) + scr[256 + et]) + scr[384 + et];
+            a.ratio[(size_t)eid[et / 5] * 5 + et % 5] = tot;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(epi_done + wi);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
 
 // T: the 16-bit operand type; APL: coefficient planes (1: the 16-bit table;
-// 2: an FP32 table as two scaled FP16 planes).
-template <typename T, int APL, bool VONLY>
+// 2: an FP32 table as two scaled FP16 planes); MODE: 0 the five outputs,
+// 1 values only, 2 the ratio contraction.
+template <typename T, int APL, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     blip_eval_tc(EvalParams p, TcArgs a, const __grid_constant__ CUtensorMap tmap,
                  const __grid_constant__ CUtensorMap tmap5)
 {
+    constexpr bool VONLY = MODE == 1;
     using Cfg = TcCfg<APL, VONLY>;
     constexpr int WPL = 2, WB = Cfg::WB, NS = Cfg::STAGES;    // WPL: weight parts (hi, lo)
     constexpr int NO = VONLY ? 1 : 5;                    // outputs per electron
@@ -352,7 +496,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *w_full = bars + 2 * NS, *w_empty = w_full + 2, *epi_done = w_full + 4;
     constexpr int kAcc = Cfg::NACC;
     uint64_t *acc_full = w_full + 6, *acc_empty = acc_full + kAcc, *drain = acc_empty + kAcc;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *red_done = drain + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(red_done + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -367,6 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(w_full + b, 1);
             mbar_init(w_empty + b, 1);
             mbar_init(epi_done + b, kEpiWarps);
+            mbar_init(red_done + b, 32 * kEpiWarps);
         }
         for (int b = 0; b < kAcc; ++b) {
             mbar_init(acc_full + b, 1);
@@ -543,7 +689,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (p.georec) bad |= p.georec[sl].bad;
                     atomicOr(p.status, bad);
                 }
+                if (MODE == 2 && et < 5) a.ratio[e * 5 + et] = nan;
                 for (int l = et; l < p.Lreal; l += 32 * kEpiWarps) {
+                    if (MODE == 2) {
+                        if (p.values) p.values[e * L + l] = nan;
+                        continue;
+                    }
                     p.values[e * L + l] = nan;
                     if (!VONLY) {
                         p.grads[e * 3 * L + l] = nan;
@@ -554,8 +705,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        if constexpr (MODE == 2) {
+            if (half == 0)
+                ratio_epilogue<0, Cfg::RLO, Cfg::ACC_COLS, kAcc>(
+                    p, a, info, wbuf, Cfg::W_BUF, w_full, acc_full, acc_empty, epi_done, red_done,
+                    tmem, q, lane, et, abort_flag);
+            else
+                ratio_epilogue<1, Cfg::RLO, Cfg::ACC_COLS, kAcc>(
+                    p, a, info, wbuf, Cfg::W_BUF, w_full, acc_full, acc_empty, epi_done, red_done,
+                    tmem, q, lane, et, abort_flag);
+        }
         long long tile = 0;
-        for (long long part = 0;; ++part) {
+        for (long long part = 0; MODE != 2; ++part) {
             const int wi = (int)(part & 1);
             if (!wait_bar(w_full + wi, (unsigned)((part >> 1) & 1), abort_flag)) {
                 if (lane == 0) raise_abort(p, abort_flag);
@@ -720,7 +881,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (bad) atomicOr(p.status, bad);
                         float **dst = info[wi].dst;
                         const size_t L = (size_t)p.Lreal;
-                        if constexpr (VONLY) {
+                        if constexpr (MODE == 2) {
+                            info[wi].eid[j] = e;
+                        } else if constexpr (VONLY) {
                             dst[j] = p.values + (size_t)e * L;
                         } else {
                             dst[5 * j] = p.values + (size_t)e * L;
@@ -820,21 +983,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <typename T, int APL, bool VONLY>
+template <typename T, int APL, int MODE>
 cudaError_t launch_tc_t(const EvalParams &p, const TcArgs &a, const CUtensorMap &tm,
                         const CUtensorMap &tm5, int sm_count, cudaStream_t stream)
 {
-    constexpr size_t smem = tc_smem<APL, VONLY>();
+    constexpr size_t smem = tc_smem<APL, MODE == 1>();
     static_assert(smem <= 227 * 1024, "stages and weight buffers exceed shared memory");
     static bool attr_set = false;   // raise this instantiation's dynamic shared-memory cap once
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(blip_eval_tc<T, APL, VONLY>,
+        cudaError_t e = cudaFuncSetAttribute(blip_eval_tc<T, APL, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int grid = std::max(1, std::min(sm_count, a.ncols));
-    blip_eval_tc<T, APL, VONLY><<<grid, kThreads, smem, stream>>>(p, a, tm, tm5);
+    blip_eval_tc<T, APL, MODE><<<grid, kThreads, smem, stream>>>(p, a, tm, tm5);
     return cudaGetLastError();
 }
 
@@ -842,8 +1005,9 @@ template <typename T, int APL>
 cudaError_t launch_tc_v(const EvalParams &p, const TcArgs &a, const CUtensorMap &tm,
                         const CUtensorMap &tm5, int sm_count, cudaStream_t stream)
 {
-    return p.grads == nullptr ? launch_tc_t<T, APL, true>(p, a, tm, tm5, sm_count, stream)
-                              : launch_tc_t<T, APL, false>(p, a, tm, tm5, sm_count, stream);
+    if (a.ratio) return launch_tc_t<T, APL, 2>(p, a, tm, tm5, sm_count, stream);
+    return p.grads == nullptr ? launch_tc_t<T, APL, 1>(p, a, tm, tm5, sm_count, stream)
+                              : launch_tc_t<T, APL, 0>(p, a, tm, tm5, sm_count, stream);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn()
@@ -955,9 +1119,11 @@ cudaError_t launch_split_pairs(const float *src, long long rows, long long row_s
 
 cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
                       int ncols, long long plane_rows, const TmaDesc &tmap, const TmaDesc *tmap5,
-                      int sm_count, int stall, cudaStream_t stream)
+                      int sm_count, int stall, cudaStream_t stream, const float *rcols,
+                      float *ratio)
 {
-    if (!p.perm || !cell_end || !cols || ncols < 1 || p.n_k || plane_rows >= (1LL << 31))
+    if (!p.perm || !cell_end || !cols || ncols < 1 || p.n_k || plane_rows >= (1LL << 31) ||
+        (ratio != nullptr) != (rcols != nullptr) || (ratio && p.grads))
         return cudaErrorInvalidValue;
     TcArgs a{};
     a.cell_end = cell_end;
@@ -968,6 +1134,8 @@ cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const 
     a.plane_rows = (int)plane_rows;
     a.stall = stall;
     a.wide = tmap5 != nullptr;
+    a.rcols = rcols;
+    a.ratio = ratio;
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(&tmap);
     const CUtensorMap &tm5 = *reinterpret_cast<const CUtensorMap *>(tmap5 ? tmap5 : &tmap);
     switch (elem) {

@@ -14,7 +14,7 @@ HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 def declared():
     src = open(HDR).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(blip_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(blip_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_binding_names():

@@ -523,7 +523,7 @@ def test_bloch_gamma_only_is_bitwise_the_plain_expansion(pb):
     with pytest.raises(pb.BlipError):
         t.set_kpoints([[0, 0, 0]], [0, 23])          # offsets must end at n_orb
     with pytest.raises(pb.BlipError):
-        t.set_kpoints([[0, 0, 0]] * 17, list(range(17)) + [24])   # at most 16 k-points
+        t.set_kpoints([[0, 0, 0]] * 65, [0] * 41 + list(range(24)) + [24])   # at most 64 k-points
     t.set_kpoints([[0.5, 0, 0]], [0, 24])
     with pytest.raises(pb.BlipError):
         t.set_kernel(2, 2, 4, 0)                      # the bulk kernel has no Bloch epilogue

@@ -181,3 +181,74 @@ def test_ratio_precision_tio2_shape(pb, storage):
                              "flipped_decisions": int(flips.sum()), "moves": len(moved),
                              "accepted_ref": int(acc_ref.sum())}))
     assert t.status() == 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_ratio_tensor_cores_dense_batch(pb, storage):
+    """A dense batch (about 3 electrons per cell, crowded cells, a NaN
+    position) in cell order goes to the tensor-core ratio: the contraction of
+    the matrix-product outputs with each electron's column, reduced on the
+    chip in a fixed order.  Checked against the FP64 oracle's contraction
+    under the tensor-core per-output bound (1.6e-5 sum_s |W_o(s)| |a_ls|, the
+    coefficient rounding of 16-bit storage, the FP16 subnormal floor) carried
+    through the column, plus the FP32 summation; the new-row output equals
+    the tensor-core evaluation's values bitwise; the CUDA-core sorted path
+    (sort = 2) meets its own bound on the same batch; repeated runs agree
+    bitwise."""
+    grid = (12, 10, 14)
+    lat = pins.triclinic_lattice()
+    n = 300                                          # 3 M tiles, the last ragged
+    tab = bi.smooth_random_table(grid, n, seed=61, sigma=2.0)
+    rng = np.random.default_rng(62)
+    ncell = int(np.prod(grid))
+    u = rng.uniform(0, 1, size=(3 * ncell, 3))
+    crowd = [(np.array(c) + rng.uniform(0.05, 0.95, size=(k, 3))) / np.array(grid)
+             for c, k in (((1, 2, 3), 60), ((5, 0, 11), 26), ((0, 9, 13), 25))]
+    u = np.concatenate([u] + crowd)
+    u[:40] += rng.integers(-5, 6, size=(40, 3))
+    pos = np.concatenate([u @ lat, [[np.nan, 1.0, 2.0]]])
+    pos = pos[rng.permutation(len(pos))]
+    E = len(pos)
+    offs = np.array([0, 1000, 1000, 3100, E], dtype=np.int32)
+    cols = rng.normal(0.0, 1.0, size=(E, n)).astype(np.float32)
+    kind = {"f32": pb.F32, "bf16": pb.BF16, "f16": pb.F16}[storage]
+    t = pb.BlipTable(grid, lat, tab, storage=kind)
+    dpos = torch.from_numpy(pos).cuda()
+    dcols = torch.from_numpy(cols).cuda()
+    doffs = torch.from_numpy(offs).cuda()
+    ratio, vals = t.eval_ratio(dpos, dcols, doffs, with_values=True, sort=1)
+    again, _ = t.eval_ratio(dpos, dcols, doffs, sort=1)
+    core, _ = t.eval_ratio(dpos, dcols, doffs, sort=2)
+    t.set_kernel(12, 1, 1, 1)
+    ev, _, _ = t.eval(dpos, doffs)
+    torch.cuda.synchronize()
+    bad = np.isnan(pos).any(1)
+    r = ratio.cpu().numpy().astype(np.float64)
+    assert np.isnan(r[bad]).all() and np.isnan(vals.cpu().numpy()[bad]).all()
+    assert torch.equal(torch.nan_to_num(ratio, nan=3.0), torch.nan_to_num(again, nan=3.0))
+    assert torch.equal(torch.nan_to_num(vals, nan=3.0), torch.nan_to_num(ev, nan=3.0))
+    ok = ~bad
+    rv, rg, rl, mag = oracle.eval_stencil(grid, lat, tab, pos[ok], absmag=True)
+    c64 = cols[ok].astype(np.float64)
+    outs = [rv, rg[:, 0], rg[:, 1], rg[:, 2], rl]
+    u_q = {"f32": 0.0, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}[storage]
+    floor = np.zeros((ok.sum(), 5, n))
+    if storage in ("f32", "f16"):
+        s_l = (2.0 if storage == "f32" else 1.0) * np.abs(tab.reshape(-1, n)).max(0)
+        ones = np.ones(tuple(grid) + (1,))
+        _, _, _, sw = oracle.eval_stencil(grid, lat, ones, pos[ok], absmag=True)
+        floor = 2.0 ** -25 * (64.0 + sw[:, :, 0])[:, :, None] * s_l[None, None, :]
+    worst = 0.0
+    for k in range(5):
+        ref = (outs[k] * c64).sum(1)
+        summ = 2 * (n / 32 + 8) * 2.0 ** -24 * np.abs(outs[k] * c64).sum(1)
+        tc_b = (np.abs(c64) * ((1.6e-5 + u_q) * mag[:, k] + floor[:, k])).sum(1) + summ + 1e-30
+        core_f = floor[:, k] if storage == "f16" else 0.0
+        core_b = (np.abs(c64) * ((TAU32 + u_q) * mag[:, k] + core_f)).sum(1) + summ + 1e-30
+        e_tc = np.abs(r[ok, k] - ref) / tc_b
+        worst = max(worst, float(e_tc.max()))
+        assert (e_tc <= 1.0).all(), (k, float(e_tc.max()))
+        e_core = np.abs(core.cpu().numpy().astype(np.float64)[ok, k] - ref)
+        assert (e_core <= core_b).all(), k
+    print(f"\nstorage {storage}: worst tensor-core ratio error / bound {worst:.3g}")
+    assert t.status() == pb.STATUS_NONFINITE_POS
