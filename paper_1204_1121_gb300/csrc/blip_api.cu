@@ -62,6 +62,7 @@ struct blip_table_s {
     // tensor-core kernel: grid-column keys in sort order, BF16 planes of an
     // FP32 table, the tensor map of its operand (made on first use)
     int *d_cols = nullptr;
+    int *d_tc_ctr = nullptr;        // tensor-core kernel: the CTAs' column counter
     int ncols = 0;
     void *d_planes = nullptr;
     float *d_tc_scales = nullptr;
@@ -284,6 +285,7 @@ int tc_prepare(blip_table_s *t)
     for (int x = 0; x < t->grid[0]; ++x)
         for (int y = 0; y < t->grid[1]; ++y) keys.push_back(sort_cell_key(t->geo, x, y, 0));
     std::sort(keys.begin(), keys.end());
+    if (!t->d_tc_ctr) CK(dev_alloc(&t->d_tc_ctr, sizeof(int)));
     if (!t->d_cols) {
         CK(dev_alloc(&t->d_cols, sizeof(int) * keys.size()));
         CK(cudaMemcpy(t->d_cols, keys.data(), sizeof(int) * keys.size(), cudaMemcpyHostToDevice));
@@ -415,7 +417,8 @@ int launch_choice(blip_table_s *t, const EvalParams &p, const KernelChoice &kc, 
         EvalParams pt = p;
         if (t->elem == ELEM_F32) pt.scales = t->d_tc_scales;   // the planes' power-of-two scales
         CK(launch_tc(pt, t->elem, cell_end, t->d_cols, t->ncols, t->rows, t->tc_tmap,
-                     t->tc_wide ? &t->tc_tmap5 : nullptr, t->sm_count, t->test_stall, stream));
+                     t->tc_wide ? &t->tc_tmap5 : nullptr, t->d_tc_ctr, t->sm_count,
+                     t->test_stall, stream));
     } else if (kc.variant == VAR_SPLIT) {
         CK(launch_split(p, t->elem, stream));
     } else if (kc.variant == VAR_REGISTER_PERSIST) {
@@ -463,7 +466,8 @@ void free_table(blip_table_s *t)
 {
     if (!t) return;
     if (!t->d_table && !t->d_scales && !t->d_status && !t->stage && !t->scratch &&
-        !t->own_stream && !t->d_cols && !t->d_planes && !t->d_tc_scales) {
+        !t->own_stream && !t->d_cols && !t->d_planes && !t->d_tc_scales &&
+        !t->d_tc_ctr) {
         delete t;
         return;
     }
@@ -480,6 +484,7 @@ void free_table(blip_table_s *t)
     if (t->stage) cudaFree(t->stage);
     if (t->scratch) cudaFree(t->scratch);
     if (t->d_cols) cudaFree(t->d_cols);
+    if (t->d_tc_ctr) cudaFree(t->d_tc_ctr);
     if (t->d_planes) cudaFree(t->d_planes);
     if (t->d_tc_scales) cudaFree(t->d_tc_scales);
     if (t->own_stream) cudaStreamDestroy(t->own_stream);
@@ -1135,8 +1140,8 @@ int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walk
         sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
         if (t->elem == ELEM_F32) p.scales = t->d_tc_scales;   // the planes' power-of-two scales
         CK(launch_tc(p, t->elem, cell_end, t->d_cols, t->ncols, t->rows, t->tc_tmap,
-                     t->tc_wide ? &t->tc_tmap5 : nullptr, t->sm_count, t->test_stall, s, inv_cols,
-                     ratio));
+                     t->tc_wide ? &t->tc_tmap5 : nullptr, t->d_tc_ctr, t->sm_count,
+                     t->test_stall, s, inv_cols, ratio));
     } else {
         CK(launch_ratio(p, t->elem, inv_cols, ratio, 4, s));
     }

@@ -200,13 +200,15 @@ cudaError_t make_tc_tmap5(const void *base, int elem, long long row_stride, int 
 // (tmap over the table, p.scales its per-component scales or null) or ELEM_F32
 // (tmap over its two FP16 planes, each plane_rows rows, p.scales their
 // power-of-two scales); tmap5: the 5-D view (or null: 1 KB boxes only);
-// cols: the ncols column keys in sort order.  Ratio mode when ratio is not
+// cols: the ncols column keys in sort order; col_ctr: one device int, the
+// CTAs' column counter (set to 0 by an async memset before the kernel).
+// Ratio mode when ratio is not
 // null: rcols [n_elec][Lreal] the inverse columns, ratio [n_elec][5] the
 // contraction, p.values the new rows or null, p.grads and p.laps null.
 cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
                       int ncols, long long plane_rows, const TmaDesc &tmap, const TmaDesc *tmap5,
-                      int sm_count, int stall, cudaStream_t stream, const float *rcols = nullptr,
-                      float *ratio = nullptr);
+                      int *col_ctr, int sm_count, int stall, cudaStream_t stream,
+                      const float *rcols = nullptr, float *ratio = nullptr);
 
 // Launch the split-stencil kernel: a block of 4 warps per (electron, chunk),
 // warp q contracting the 16 sites of a_1 slab q, partial sums added in a

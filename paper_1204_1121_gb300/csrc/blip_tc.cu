@@ -24,16 +24,20 @@
 // lo.lo, below 2^-22 relative; s_l is applied in the epilogue.  Products are
 // accumulated in FP32 in tensor memory.
 //
-// Persistent grid, one CTA per SM, 14 warps:
-//   warp 0      TMA producer: per (part, M tile, plane) the 16 stencil
+// Persistent grid, one CTA per SM, 14 warps; the CTAs take grid columns
+// from a work queue (a global counter over the columns in sort order):
+//   warp 0      takes the columns (skipping empty ones) and passes them to
+//               the weight warps through a 4-slot ring; TMA producer: per
+//               (part, M tile, plane) the 16 stencil
 //               columns x 2 halves of 8 rows x 64 components into a 3-stage
 //               ring, as 4 boxes of 8 KB (4 consecutive grid columns x 2
 //               halves, a 5-D view of the table) or, where the columns wrap
 //               around the cell, 32 boxes of 1 KB;
 //   warp 1      allocates tensor memory and issues the MMAs (one thread):
-//               per M tile, 8 K steps x planes products into one of four
-//               128-column FP32 accumulators, then tcgen05.commit to the
-//               stage's empty barrier and the accumulator's full barrier;
+//               per M tile, 8 K steps x planes products into one of the
+//               FP32 accumulators (two of 256 columns, four of 64 for
+//               values only), then tcgen05.commit to the stage's empty
+//               barrier and the accumulator's full barrier;
 //   warps 2-9   epilogue, two warps per lane quarter of the accumulator:
 //               tensor memory -> registers (tcgen05.ld), scale, streaming
 //               stores through a per-column output-row pointer (a warp
@@ -81,6 +85,7 @@ constexpr int kThreads = 32 * (2 + kEpiWarps + 4);
 constexpr uint32_t kBox = 1024;                          // 8 rows x 128 bytes
 constexpr uint32_t kStage = kMT * kK * 2;                // one operand plane of one M tile: 32 KB
 constexpr uint32_t kTmemCols = 512;                      // all of tensor memory
+constexpr int kColQ = 4;                                 // column ring slots
 
 // Shapes of one instantiation: APL coefficient planes per M tile (1: the
 // 16-bit table as stored; 2: an FP32 table as two FP16 planes, hi + lo, of
@@ -123,6 +128,7 @@ struct TcArgs {
     int plane_rows;        // rows of one coefficient plane in the tensor map
     int stall;             // test hook: the MMA thread never releases the first stage
     int wide;              // 1: the 5-D tensor map (8 KB boxes) is usable
+    int *col_ctr;          // work queue: the next column to take (0 at launch)
     const float *rcols;    // ratio mode: [n_elec][Lreal] inverse columns, else null
     float *ratio;          // ratio mode: [n_elec][5] output, else null
 };
@@ -131,7 +137,7 @@ template <int APL, bool VONLY>
 constexpr size_t tc_smem()
 {
     using C = TcCfg<APL, VONLY>;
-    return C::STAGES * kStage + C::WB * C::W_BUF + 2 * sizeof(PartInfo) + 256;
+    return C::STAGES * kStage + C::WB * C::W_BUF + 2 * sizeof(PartInfo) + 512;
 }
 
 // ---------------------------------------------------------------------------
@@ -497,8 +503,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int kAcc = Cfg::NACC;
     uint64_t *acc_full = w_full + 6, *acc_empty = acc_full + kAcc, *drain = acc_empty + kAcc;
     uint64_t *red_done = drain + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(red_done + 2);
+    uint64_t *cq_full = red_done + 2, *cq_empty = cq_full + kColQ;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cq_empty + kColQ);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *colq = abort_flag + 1;           // the column ring
+    volatile int *decision = colq + kColQ;         // weight warps: 1 = stop
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n2 = p.geo.n[1], n3 = p.geo.n[2];
@@ -519,6 +528,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(acc_empty + b, kEpiWarps);
         }
         mbar_init(drain, 1);
+        for (int q = 0; q < kColQ; ++q) {
+            mbar_init(cq_full + q, 1);
+            mbar_init(cq_empty + q, 4);              // the four weight warps
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -542,7 +555,54 @@ __global__ void __launch_bounds__(kThreads, 1)
         // kx 8 KB + h 4 KB + ky 1 KB (one 128-byte-swizzled 8-row atom each)
         const int c = lane >> 1, h = lane & 1;     // narrow boxes: column c, half h
         const int kxl = c >> 2, kyl = c & 3;
-        for (int ci = blockIdx.x; ci < a.ncols && ok; ci += gridDim.x) {
+        // Columns come from a work queue shared by the CTAs (a global counter,
+        // so the CTAs stay on neighbouring columns in sort order and each
+        // takes more as it finishes); each taken column goes into the ring
+        // for the weight warps, two columns ahead of this warp's own use
+        // (the weight warps run at most two parts ahead of it).
+        int pushed = 0;
+        bool more = true;
+        auto push = [&]() -> int {                   // column, -1 at the end, -2 on abort
+            if (!more) return -1;
+            const int slot = pushed % kColQ;
+            if (pushed >= kColQ) {
+                const bool got = wait_bar(cq_empty + slot, (unsigned)(((pushed / kColQ) - 1) & 1),
+                                          abort_flag);
+                if (!__all_sync(FULL, got)) {
+                    if (lane == 0) raise_abort(p, abort_flag);
+                    return -2;
+                }
+            }
+            int col = 0;
+            if (lane == 0) {
+                // columns without electrons are skipped here, so every column
+                // in the ring has a part: the weight warps, at most two parts
+                // ahead of this warp, never wait for a column it has not pushed
+                for (;;) {
+                    col = atomicAdd(a.col_ctr, 1);
+                    if (col >= a.ncols) break;
+                    const int kc = a.cols[col];
+                    if (a.cell_end[kc + n3 - 1] > (kc ? a.cell_end[kc - 1] : 0)) break;
+                }
+                colq[slot] = col < a.ncols ? col : -1;
+                mbar_arrive(cq_full + slot);
+            }
+            col = __shfl_sync(FULL, col, 0);
+            ++pushed;
+            if (col >= a.ncols) {
+                more = false;
+                return -1;
+            }
+            return col;
+        };
+        int q0 = push(), q1 = push();
+        ok = q0 != -2 && q1 != -2;
+        while (ok && q0 >= 0) {
+            const int q2 = push();
+            if (q2 == -2) break;
+            const int ci = q0;
+            q0 = q1;
+            q1 = q2;
             const int k0 = a.cols[ci];
             int x, y;
             column_xy(p.geo, k0, x, y);
@@ -596,50 +656,49 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         // ---------------- MMA issue (one thread) ----------------
-        long long fill = 0, tile = 0;
-        bool ok = true;
-        const uint32_t stage_base = smem_addr(stageA), w_base = smem_addr(wbuf);
-        for (long long part = 0; ok; ++part) {
-            const int wi = (int)(part & 1);                  // info slot
-            const int wb = WB == 2 ? wi : 0;                 // weight buffer
-            if (!wait_bar(w_full + wi, (unsigned)((part >> 1) & 1), abort_flag)) {
-                if (lane == 0) raise_abort(p, abort_flag);
-                break;
-            }
-            if (info[wi].cnt < 0) break;
-            const int nh = info[wi].n;                       // rows of one weight part
-            const uint32_t id_both = instr_desc(Cfg::RLO + nh, FMT);   // hi and lo parts
-            const uint32_t id_hi = instr_desc(nh, FMT);                 // hi part only
-            const uint32_t sw = w_base + wb * Cfg::W_BUF;
-            for (int m = 0; m < a.mt && ok; ++m) {
-                const int ab = (int)(tile % kAcc);
-                if (tile >= kAcc) {
-                    const bool got = wait_bar(acc_empty + ab, (unsigned)(((tile / kAcc) - 1) & 1), abort_flag);
-                    if (!__all_sync(FULL, got)) {
-                        if (lane == 0) raise_abort(p, abort_flag);
-                        ok = false;
-                        break;
-                    }
+        // lane 0 alone: no warp votes or warp barriers between the products
+        // of consecutive stages, so the tensor pipe's short queue stays fed
+        if (lane == 0) {
+            long long fill = 0, tile = 0;
+            bool ok = true;
+            const uint32_t stage_base = smem_addr(stageA), w_base = smem_addr(wbuf);
+            for (long long part = 0; ok; ++part) {
+                const int wi = (int)(part & 1);                  // info slot
+                const int wb = WB == 2 ? wi : 0;                 // weight buffer
+                if (!wait_bar(w_full + wi, (unsigned)((part >> 1) & 1), abort_flag)) {
+                    raise_abort(p, abort_flag);
+                    break;
                 }
-                const uint32_t d = tmem + (uint32_t)(ab * Cfg::ACC_COLS);
-                // the hi plane first: its product (N = RLO + NH) sets every
-                // column the epilogue reads; the lo plane's (N = NH) adds
-                for (int pl = 0; pl < APL; ++pl) {
-                    const int s = (int)(fill % NS);
-                    const bool got = wait_bar(a_full + s, (unsigned)((fill / NS) & 1), abort_flag);
-                    if (!__all_sync(FULL, got)) {
-                        if (lane == 0) raise_abort(p, abort_flag);
+                if (info[wi].cnt < 0) break;
+                const int nh = info[wi].n;                       // rows of one weight part
+                const uint32_t id_both = instr_desc(Cfg::RLO + nh, FMT);   // hi and lo parts
+                const uint32_t id_hi = instr_desc(nh, FMT);                 // hi part only
+                const uint32_t sw = w_base + wb * Cfg::W_BUF;
+                for (int m = 0; m < a.mt && ok; ++m) {
+                    const int ab = (int)(tile % kAcc);
+                    if (tile >= kAcc &&
+                        !wait_bar(acc_empty + ab, (unsigned)(((tile / kAcc) - 1) & 1), abort_flag)) {
+                        raise_abort(p, abort_flag);
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    if (lane == 0) {
+                    const uint32_t d = tmem + (uint32_t)(ab * Cfg::ACC_COLS);
+                    // the hi plane first: its product (N = RLO + NH) sets every
+                    // column the epilogue reads; the lo plane's (N = NH) adds
+                    for (int pl = 0; pl < APL; ++pl) {
+                        const int s = (int)(fill % NS);
+                        if (!wait_bar(a_full + s, (unsigned)((fill / NS) & 1), abort_flag)) {
+                            raise_abort(p, abort_flag);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
                         const uint32_t sa = stage_base + s * kStage;
                         // a 16-bit table (pl = 0) meets both weight parts in one
                         // product; of an FP32 table's planes the lo one meets the
                         // hi weights only (lo x lo is below 2^-22 relative)
                         const uint32_t id = (APL == 2 && pl == 1) ? id_hi : id_both;
-#pragma unroll 1
+#pragma unroll
                         for (int ks = 0; ks < kK / 16; ++ks) {
                             // A: K step ks = stencil columns (kx, ky), (kx, ky + 1)
                             // with kx = ks / 2, ky = 2 (ks % 2): 1 KB apart, the
@@ -655,16 +714,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mma_commit(acc_full + ab);
                             if (m == a.mt - 1) mma_commit(w_empty + wi);
                         }
+                        ++fill;
                     }
-                    __syncwarp();
-                    ++fill;
+                    if (ok) ++tile;
                 }
-                if (ok) ++tile;
             }
-        }
-        // every product issued (also those of a tile cut short by an abort)
-        // must be done before the tensor memory is freed
-        if (lane == 0) {
+            // every product issued (also those of a tile cut short by an abort)
+            // must be done before the tensor memory is freed
             mma_commit(drain);
             if (!mbar_wait(drain, 0)) atomicOr(p.status, BLIP_STATUS_TIMEOUT);
         }
@@ -789,26 +845,44 @@ __global__ void __launch_bounds__(kThreads, 1)
                 got = wait_bar(w_empty + (int)(pp & 1), (unsigned)((pp >> 1) & 1), abort_flag);
             }
             if (!__all_sync(FULL, got) && lane == 0) raise_abort(p, abort_flag);
+            // one thread reads the abort flag between two barriers, so the four
+            // warps take the same decision (and meet the same barriers after it)
             named_sync(1, 128);
-            return !*abort_flag;
+            if (ww == 0 && lane == 0) *decision = *abort_flag;
+            named_sync(1, 128);
+            return !*decision;
         };
         const float *J = p.geo.J, *M = p.geo.M;
         const float nrm = p.geo.norm;
         // the parts of this CTA's columns in order, one part ahead: the next
         // part's electron records are loaded while this part's weights are
         // built (their latency was the weight warps' main cost)
-        int ci = blockIdx.x;
+        int taken = 0;
+        auto take = [&]() -> int {                   // the producer's next column, -1 at the end
+            const int slot = taken % kColQ;
+            const bool got = wait_bar(cq_full + slot, (unsigned)((taken / kColQ) & 1), abort_flag);
+            if (!__all_sync(FULL, got)) {
+                if (lane == 0) raise_abort(p, abort_flag);
+                return -1;
+            }
+            const int col = colq[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(cq_empty + slot);
+            ++taken;
+            return col;
+        };
+        int ci = take();
         Cursor cur;
         ColumnEnds ends;
-        if (ci < a.ncols) {
+        if (ci >= 0) {
             cursor_init(a, a.cols[ci], cur);
             ends_init(a, a.cols[ci], n3, lane, ends);
         }
         auto advance = [&](int &z0_, int &s0_, int &cnt_) -> bool {
-            while (ci < a.ncols) {
+            while (ci >= 0) {
                 if (next_part(a, n3, lane, ends, cur, z0_, s0_, cnt_)) return true;
-                ci += gridDim.x;
-                if (ci < a.ncols) {
+                ci = take();
+                if (ci >= 0) {
                     cursor_init(a, a.cols[ci], cur);
                     ends_init(a, a.cols[ci], n3, lane, ends);
                 }
@@ -997,6 +1071,9 @@ cudaError_t launch_tc_t(const EvalParams &p, const TcArgs &a, const CUtensorMap 
         attr_set = true;
     }
     const int grid = std::max(1, std::min(sm_count, a.ncols));
+    // the column counter of the CTAs' work queue starts at 0
+    cudaError_t e = cudaMemsetAsync(a.col_ctr, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
     blip_eval_tc<T, APL, MODE><<<grid, kThreads, smem, stream>>>(p, a, tm, tm5);
     return cudaGetLastError();
 }
@@ -1119,10 +1196,10 @@ cudaError_t launch_split_pairs(const float *src, long long rows, long long row_s
 
 cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
                       int ncols, long long plane_rows, const TmaDesc &tmap, const TmaDesc *tmap5,
-                      int sm_count, int stall, cudaStream_t stream, const float *rcols,
-                      float *ratio)
+                      int *col_ctr, int sm_count, int stall, cudaStream_t stream,
+                      const float *rcols, float *ratio)
 {
-    if (!p.perm || !cell_end || !cols || ncols < 1 || p.n_k || plane_rows >= (1LL << 31) ||
+    if (!p.perm || !cell_end || !cols || !col_ctr || ncols < 1 || p.n_k || plane_rows >= (1LL << 31) ||
         (ratio != nullptr) != (rcols != nullptr) || (ratio && p.grads))
         return cudaErrorInvalidValue;
     TcArgs a{};
@@ -1134,6 +1211,7 @@ cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const 
     a.plane_rows = (int)plane_rows;
     a.stall = stall;
     a.wide = tmap5 != nullptr;
+    a.col_ctr = col_ctr;
     a.rcols = rcols;
     a.ratio = ratio;
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(&tmap);
