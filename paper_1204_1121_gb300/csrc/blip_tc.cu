@@ -659,11 +659,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         // lane 0 alone: no warp votes or warp barriers between the products
         // of consecutive stages, so the tensor pipe's short queue stays fed
         if (lane == 0) {
-            long long fill = 0, tile = 0;
-            bool ok = true;
-            const uint32_t stage_base = smem_addr(stageA), w_base = smem_addr(wbuf);
-            for (long long part = 0; ok; ++part) {
-                const int wi = (int)(part & 1);                  // info slot
+            // A single thread runs this loop, so every instruction's latency
+            // counts: ring positions and parities are kept incrementally, and
+            // the descriptors are those of stage 0 / weight buffer 0 plus the
+            // byte offset / 16 (the 14-bit address field cannot carry: shared
+            // addresses stay below 2^18)
+            bool ok = true, first = true;
+            int s = 0, s_ph = 0;                     // stage ring slot, its fill parity
+            int ab = 0, ab_ph = 0, tiles = 0;        // accumulator slot, its round parity
+            const uint64_t a_desc0 = smem_desc(smem_addr(stageA), 4096u, kBox, 2);
+            const uint64_t b_desc0 = smem_desc(smem_addr(wbuf), Cfg::KGROUP, 128u, 0);
+            for (int part = 0; ok; ++part) {
+                const int wi = part & 1;                         // info slot
                 const int wb = WB == 2 ? wi : 0;                 // weight buffer
                 if (!wait_bar(w_full + wi, (unsigned)((part >> 1) & 1), abort_flag)) {
                     raise_abort(p, abort_flag);
@@ -673,11 +680,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int nh = info[wi].n;                       // rows of one weight part
                 const uint32_t id_both = instr_desc(Cfg::RLO + nh, FMT);   // hi and lo parts
                 const uint32_t id_hi = instr_desc(nh, FMT);                 // hi part only
-                const uint32_t sw = w_base + wb * Cfg::W_BUF;
+                const uint64_t bd0 = b_desc0 + (uint64_t)((wb * Cfg::W_BUF) >> 4);
                 for (int m = 0; m < a.mt && ok; ++m) {
-                    const int ab = (int)(tile % kAcc);
-                    if (tile >= kAcc &&
-                        !wait_bar(acc_empty + ab, (unsigned)(((tile / kAcc) - 1) & 1), abort_flag)) {
+                    if (tiles >= kAcc &&
+                        !wait_bar(acc_empty + ab, (unsigned)(ab_ph ^ 1), abort_flag)) {
                         raise_abort(p, abort_flag);
                         ok = false;
                         break;
@@ -686,14 +692,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // the hi plane first: its product (N = RLO + NH) sets every
                     // column the epilogue reads; the lo plane's (N = NH) adds
                     for (int pl = 0; pl < APL; ++pl) {
-                        const int s = (int)(fill % NS);
-                        if (!wait_bar(a_full + s, (unsigned)((fill / NS) & 1), abort_flag)) {
+                        if (!wait_bar(a_full + s, (unsigned)s_ph, abort_flag)) {
                             raise_abort(p, abort_flag);
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = stage_base + s * kStage;
+                        const uint64_t ad0 = a_desc0 + (uint64_t)((s * kStage) >> 4);
                         // a 16-bit table (pl = 0) meets both weight parts in one
                         // product; of an FP32 table's planes the lo one meets the
                         // hi weights only (lo x lo is below 2^-22 relative)
@@ -704,19 +709,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // with kx = ks / 2, ky = 2 (ks % 2): 1 KB apart, the
                             // second 64-component half 4 KB on; B: K groups of 8
                             // at KGROUP bytes, N groups of 8 rows at 128 B
-                            const uint64_t ad = smem_desc(sa + (ks >> 1) * 8192 + (ks & 1) * 2 * kBox,
-                                                          4096u, kBox, 2);
-                            const uint64_t bd = smem_desc(sw + ks * 2 * Cfg::KGROUP, Cfg::KGROUP, 128u, 0);
+                            const uint64_t ad =
+                                ad0 + (uint64_t)(((ks >> 1) * 8192 + (ks & 1) * 2 * kBox) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)((ks * 2 * Cfg::KGROUP) >> 4);
                             mma_f16(d, ad, bd, id, (pl == 0 && ks == 0) ? 0u : 1u);
                         }
-                        if (!(a.stall && fill == 0)) mma_commit(a_empty + s);
+                        if (!(a.stall && first)) mma_commit(a_empty + s);
+                        first = false;
                         if (pl == APL - 1) {
                             mma_commit(acc_full + ab);
                             if (m == a.mt - 1) mma_commit(w_empty + wi);
                         }
-                        ++fill;
+                        if (++s == NS) {
+                            s = 0;
+                            s_ph ^= 1;
+                        }
                     }
-                    if (ok) ++tile;
+                    if (ok) {
+                        ++tiles;
+                        if (++ab == kAcc) {
+                            ab = 0;
+                            ab_ph ^= 1;
+                        }
+                    }
                 }
             }
             // every product issued (also those of a tile cut short by an abort)
