@@ -63,11 +63,14 @@ struct blip_table_s {
     // FP32 table, the tensor map of its operand (made on first use)
     int *d_cols = nullptr;
     int *d_tc_ctr = nullptr;        // tensor-core kernel: the CTAs' column counter
+    float *d_rsig = nullptr;        // ratio kernel: per-electron column scales
+    int rsig_n = 0;
     int ncols = 0;
     void *d_planes = nullptr;
     float *d_tc_scales = nullptr;
     TmaDesc tc_tmap = {};
     TmaDesc tc_tmap5 = {};
+    TmaDesc tc_tmap5k = {};         // the same view with one slab per box (ratio kernel)
     bool tc_wide = false;
     bool tc_ready = false;
     // L2 residency: access-policy window over the table (bytes, 0 = off) and
@@ -315,8 +318,11 @@ int tc_prepare(blip_table_s *t)
     CK(make_tc_tmap(operand, op_elem, t->row_stride, rows_total, &t->tc_tmap));
     // the 5-D view for 8 KB boxes; without it the kernel uses 1 KB boxes only
     t->tc_wide = make_tc_tmap5(operand, op_elem, t->row_stride, t->grid[0] * t->grid[1],
-                               t->grid[2], t->elem == ELEM_F32 ? 2 : 1, t->rows,
-                               &t->tc_tmap5) == cudaSuccess;
+                               t->grid[2], t->elem == ELEM_F32 ? 2 : 1, t->rows, 2,
+                               &t->tc_tmap5) == cudaSuccess &&
+                 make_tc_tmap5(operand, op_elem, t->row_stride, t->grid[0] * t->grid[1],
+                               t->grid[2], t->elem == ELEM_F32 ? 2 : 1, t->rows, 1,
+                               &t->tc_tmap5k) == cudaSuccess;
     t->tc_ready = true;
     return BLIP_OK;
 }
@@ -467,7 +473,7 @@ void free_table(blip_table_s *t)
     if (!t) return;
     if (!t->d_table && !t->d_scales && !t->d_status && !t->stage && !t->scratch &&
         !t->own_stream && !t->d_cols && !t->d_planes && !t->d_tc_scales &&
-        !t->d_tc_ctr) {
+        !t->d_tc_ctr && !t->d_rsig) {
         delete t;
         return;
     }
@@ -485,6 +491,7 @@ void free_table(blip_table_s *t)
     if (t->scratch) cudaFree(t->scratch);
     if (t->d_cols) cudaFree(t->d_cols);
     if (t->d_tc_ctr) cudaFree(t->d_tc_ctr);
+    if (t->d_rsig) cudaFree(t->d_rsig);
     if (t->d_planes) cudaFree(t->d_planes);
     if (t->d_tc_scales) cudaFree(t->d_tc_scales);
     if (t->own_stream) cudaStreamDestroy(t->own_stream);
@@ -1135,7 +1142,27 @@ int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walk
             tc = rc == BLIP_OK;
         }
     }
-    if (tc) {
+    // the ratio kernel's per-electron column scales (FP16 operands)
+    if (tc && !values && t->elem != ELEM_BF16 && t->rsig_n < n_elec) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            if (t->d_rsig) cudaFree(t->d_rsig);
+            t->d_rsig = nullptr;
+            t->rsig_n = 0;
+            CK(dev_alloc(&t->d_rsig, sizeof(float) * (size_t)n_elec));
+            t->rsig_n = n_elec;
+        }
+    }
+    if (tc && !values && (t->elem == ELEM_BF16 || t->rsig_n >= n_elec)) {
+        // the orbital sum on the tensor cores, inverse columns as an operand
+        const int *keys = nullptr, *cell_end = nullptr;
+        sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
+        if (t->elem == ELEM_F32) p.scales = t->d_tc_scales;   // the planes' power-of-two scales
+        CK(launch_ratio_tc(p, t->elem, cell_end, t->d_cols, t->ncols, t->rows, t->tc_tmap,
+                           t->tc_wide ? &t->tc_tmap5k : nullptr, t->d_tc_ctr, t->sm_count,
+                           t->test_stall, s, inv_cols, ratio, t->d_rsig));
+    } else if (tc) {
         const int *keys = nullptr, *cell_end = nullptr;
         sort_views(t->geo, n_elec, t->scratch, &keys, &cell_end);
         if (t->elem == ELEM_F32) p.scales = t->d_tc_scales;   // the planes' power-of-two scales

@@ -191,11 +191,13 @@ cudaError_t make_tc_tmap(const void *base, int elem, long long row_stride, long 
 // row_stride words.
 cudaError_t launch_split_pairs(const float *src, long long rows, long long row_stride, int Lreal,
                               unsigned int *bits, float *scales, void *dst, cudaStream_t stream);
-// The 5-D view of the same operand for 8 KB boxes: components within a
+// The 5-D view of the same operand for wide boxes: components within a
 // 64-component slab, rows of a grid column (n3 + 3), grid columns (n1 n2),
-// slabs, planes; box 64 x 8 x 4 x 2 x 1.
+// slabs, planes; box 64 x 8 x 4 x box_slabs x 1 (box_slabs 2: the 8 KB boxes
+// of the evaluation kernel; 1: the 4 KB boxes of the ratio kernel's K-major
+// stages).
 cudaError_t make_tc_tmap5(const void *base, int elem, long long row_stride, int n12, int n3,
-                          int planes, long long plane_rows, TmaDesc *out);
+                          int planes, long long plane_rows, int box_slabs, TmaDesc *out);
 // Launch the tensor-core kernel (needs the sort): elem = ELEM_BF16 / ELEM_F16
 // (tmap over the table, p.scales its per-component scales or null) or ELEM_F32
 // (tmap over its two FP16 planes, each plane_rows rows, p.scales their
@@ -209,6 +211,17 @@ cudaError_t launch_tc(const EvalParams &p, int elem, const int *cell_end, const 
                       int ncols, long long plane_rows, const TmaDesc &tmap, const TmaDesc *tmap5,
                       int *col_ctr, int sm_count, int stall, cudaStream_t stream,
                       const float *rcols = nullptr, float *ratio = nullptr);
+
+// Launch the tensor-core ratio kernel (blip_ratio_tc.cu; needs the sort, as
+// launch_tc): ratio [n_elec][5] = the contraction of each electron's orbital
+// outputs with its column rcols [n_elec][Lreal], the orbital sum on the
+// tensor cores; p.values, p.grads and p.laps null.  tmap5k: the 5-D view with
+// box_slabs 1 (or null: 1 KB boxes only).  sig: device scratch of n_elec
+// floats (the columns' scales, written by a pre-pass; unused for BF16).
+cudaError_t launch_ratio_tc(const EvalParams &p, int elem, const int *cell_end, const int *cols,
+                            int ncols, long long plane_rows, const TmaDesc &tmap,
+                            const TmaDesc *tmap5k, int *col_ctr, int sm_count, int stall,
+                            cudaStream_t stream, const float *rcols, float *ratio, float *sig);
 
 // Launch the split-stencil kernel: a block of 4 warps per (electron, chunk),
 // warp q contracting the 16 sites of a_1 slab q, partial sums added in a

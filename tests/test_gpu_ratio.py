@@ -217,7 +217,7 @@ def test_ratio_tensor_cores_dense_batch(pb, storage):
     dcols = torch.from_numpy(cols).cuda()
     doffs = torch.from_numpy(offs).cuda()
     ratio, vals = t.eval_ratio(dpos, dcols, doffs, with_values=True, sort=1)
-    again, _ = t.eval_ratio(dpos, dcols, doffs, sort=1)
+    again, _ = t.eval_ratio(dpos, dcols, doffs, with_values=True, sort=1)
     core, _ = t.eval_ratio(dpos, dcols, doffs, sort=2)
     t.set_kernel(12, 1, 1, 1)
     ev, _, _ = t.eval(dpos, doffs)
@@ -251,4 +251,86 @@ def test_ratio_tensor_cores_dense_batch(pb, storage):
         e_core = np.abs(core.cpu().numpy().astype(np.float64)[ok, k] - ref)
         assert (e_core <= core_b).all(), k
     print(f"\nstorage {storage}: worst tensor-core ratio error / bound {worst:.3g}")
+    assert t.status() == pb.STATUS_NONFINITE_POS
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_ratio_tensor_core_operand_kernel(pb, storage):
+    """Without the new-row output, a dense batch in cell order goes to the
+    ratio kernel that contracts the orbitals on the tensor cores first,
+    Y[k][j] = sum_l a[k][l] c_j[l] over the part's 128 union rows k, then
+    sum_k W_o^(j)[k] Y[k][j] in the epilogue.  Its bound: the tensor-core
+    coefficient bound (1.6e-5 C_o, storage rounding, FP16 subnormal floor)
+    carried through the column; the FP32 accumulation over the 16 L/128
+    K steps and the 64-term reduction, (16 L/128 + 16) 2^-24 sum_l |c_l|
+    C_o(l); the 16-bit split of c'_l = c_l s_l / sigma (FP16: 2^-22 relative
+    plus 2^-25 sigma absolute, sigma the power of two at or above
+    max_l |c_l s_l|; BF16: 2^-17 relative), carried through |psi_l|; and the
+    FP32 summation term of the other tests.  Repeated runs agree bitwise;
+    with the new-row output requested the evaluation kernel's ratio epilogue
+    runs instead and also meets its bound."""
+    grid = (12, 10, 14)
+    lat = pins.triclinic_lattice()
+    n = 300
+    tab = bi.smooth_random_table(grid, n, seed=63, sigma=2.0)
+    rng = np.random.default_rng(64)
+    ncell = int(np.prod(grid))
+    u = rng.uniform(0, 1, size=(3 * ncell, 3))
+    crowd = [(np.array(c) + rng.uniform(0.05, 0.95, size=(k, 3))) / np.array(grid)
+             for c, k in (((2, 3, 4), 40), ((7, 1, 0), 26), ((11, 9, 13), 25))]
+    u = np.concatenate([u] + crowd)
+    u[:40] += rng.integers(-5, 6, size=(40, 3))
+    pos = np.concatenate([u @ lat, [[1.0, np.inf, 2.0]]])
+    pos = pos[rng.permutation(len(pos))]
+    E = len(pos)
+    # columns of mixed magnitude per electron (the per-electron scale sigma)
+    cols = (rng.normal(0.0, 1.0, size=(E, n)) *
+            10.0 ** rng.uniform(-3, 3, size=(E, 1))).astype(np.float32)
+    kind = {"f32": pb.F32, "bf16": pb.BF16, "f16": pb.F16}[storage]
+    t = pb.BlipTable(grid, lat, tab, storage=kind)
+    dpos = torch.from_numpy(pos).cuda()
+    dcols = torch.from_numpy(cols).cuda()
+    r1, _ = t.eval_ratio(dpos, dcols, sort=1)
+    r2, _ = t.eval_ratio(dpos, dcols, sort=1)
+    rv_, _ = t.eval_ratio(dpos, dcols, with_values=True, sort=1)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.nan_to_num(r1, nan=3.0), torch.nan_to_num(r2, nan=3.0))
+    bad = ~np.isfinite(pos).all(1)
+    r = r1.cpu().numpy().astype(np.float64)
+    assert np.isnan(r[bad]).all()
+    ok = ~bad
+    rv, rg, rl, mag = oracle.eval_stencil(grid, lat, tab, pos[ok], absmag=True)
+    c64 = cols[ok].astype(np.float64)
+    outs = [rv, rg[:, 0], rg[:, 1], rg[:, 2], rl]
+    u_q = {"f32": 0.0, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}[storage]
+    amax = np.abs(tab.reshape(-1, n)).max(0)
+    s_l = 2.0 ** np.ceil(np.log2(amax)) if storage == "f32" else amax
+    floor = np.zeros((ok.sum(), 5, n))
+    if storage in ("f32", "f16"):
+        ones = np.ones(tuple(grid) + (1,))
+        _, _, _, sw = oracle.eval_stencil(grid, lat, ones, pos[ok], absmag=True)
+        floor = 2.0 ** -25 * (64.0 + sw[:, :, 0])[:, :, None] * \
+            ((2.0 if storage == "f32" else 1.0) * amax)[None, None, :]
+    sig = 2.0 ** np.ceil(np.log2(np.abs(c64 * s_l[None, :]).max(1)))
+    mt = (n + 127) // 128
+    worst = 0.0
+    rw = rv_.cpu().numpy().astype(np.float64)
+    for k in range(5):
+        ref = (outs[k] * c64).sum(1)
+        summ = 2 * (n / 32 + 8) * 2.0 ** -24 * np.abs(outs[k] * c64).sum(1)
+        base = (np.abs(c64) * ((1.6e-5 + u_q) * mag[:, k] + floor[:, k])).sum(1)
+        acc = (16 * mt + 16) * 2.0 ** -24 * (np.abs(c64) * mag[:, k]).sum(1)
+        if storage == "bf16":
+            split = 2.0 ** -17 * (np.abs(outs[k]) * np.abs(c64)).sum(1)
+        else:
+            split = (np.abs(outs[k]) * (2.0 ** -22 * np.abs(c64) +
+                                        2.0 ** -25 * sig[:, None] / s_l[None, :])).sum(1)
+        bound = base + acc + split + summ + 1e-30
+        e = np.abs(r[ok, k] - ref) / bound
+        worst = max(worst, float(e.max()))
+        assert (e <= 1.0).all(), (k, float(e.max()))
+        # the evaluation kernel's ratio epilogue (new rows requested)
+        eb = (np.abs(c64) * ((1.6e-5 + u_q) * mag[:, k] + floor[:, k])).sum(1) + summ + 1e-30
+        assert (np.abs(rw[ok, k] - ref) <= eb).all(), k
+    print(f"\nstorage {storage}: worst operand-kernel ratio error / bound {worst:.3g}")
     assert t.status() == pb.STATUS_NONFINITE_POS
