@@ -229,10 +229,13 @@ class BlipTable:
                                         P(ptr(lp)) if lp is not None else None), "blip_eval_host")
         return v, g, lp
 
-    def eval_ratio(self, pos, inv_cols, offsets=None, with_values=False, sort=0, stream=None):
+    def eval_ratio(self, pos, inv_cols, offsets=None, with_values=False, sort=0, stream=None,
+                   values_out=None):
         """Fused ratio (``blip_eval_ratio``): returns (ratio [E][5], values or
         None).  ``inv_cols``: CUDA float32 [E][n_orb], column j of the inverse
-        Slater matrix for electron j."""
+        Slater matrix for electron j; ``values_out``: a preallocated
+        [E][n_orb] float32 CUDA tensor for the new rows (implies
+        with_values)."""
         import torch
         if not (pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous()):
             raise TypeError("pos must be a contiguous CUDA float64 tensor")
@@ -240,8 +243,14 @@ class BlipTable:
             raise TypeError("inv_cols must be a contiguous CUDA float32 tensor")
         n = pos.shape[0]
         ratio = torch.empty((n, 5), dtype=torch.float32, device=pos.device)
-        vals = torch.empty((n, self.Lreal), dtype=torch.float32, device=pos.device) \
-            if with_values else None
+        if values_out is not None:
+            if not (values_out.is_cuda and values_out.dtype == torch.float32 and
+                    values_out.is_contiguous() and values_out.numel() >= n * self.Lreal):
+                raise TypeError("values_out must be a contiguous CUDA float32 tensor of E x n_orb")
+            vals = values_out
+        else:
+            vals = torch.empty((n, self.Lreal), dtype=torch.float32, device=pos.device) \
+                if with_values else None
         nw = 0 if offsets is None else offsets.shape[0] - 1
         _check(self._lib.blip_eval_ratio(self._h, P(pos.data_ptr()), n,
                                          P(offsets.data_ptr()) if offsets is not None else None,
