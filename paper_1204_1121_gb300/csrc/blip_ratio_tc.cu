@@ -27,24 +27,24 @@
 // component's scale, sigma_j a power of two at or above max_l |c_j[l] s_l|
 // for FP16 operands, from a pre-pass over the columns; 1 for BF16) split
 // into two 16-bit parts (hi + lo) stacked along N (rows 0..31 hi, 32..63
-// lo), built on the chip per orbital tile into a 4-slot ring from column
-// segments that the producer stages in shared memory by bulk copies (or,
-// for columns not 16-byte aligned, read from global memory).  FP32 tables enter as their two scaled FP16
+// lo), built on the chip per orbital tile into a 4-slot ring by 8 warps
+// from the columns in global memory (asked into L2 one part ahead).  One
+// bulk copy per electron and tile would be the obvious staging, but the copy
+// engine then issues ~30 small copies per tile and binds the kernel.  FP32 tables enter as their two scaled FP16
 // planes: hi plane x (hi + lo), lo plane x hi.
 //
 // Persistent grid, one CTA per SM, 14 warps, the columns from the shared
 // work queue of the evaluation kernel:
 //   warp 0      takes columns, passes them on through a 4-slot ring; TMA
-//               producer of the table tiles (3-stage ring) and of the
-//               column segments (2 slots, one bulk copy per electron);
+//               producer of the table tiles (4-stage ring);
 //   warp 1      tensor memory and the MMAs (one thread): per part and
 //               orbital tile, 8 K steps x planes into the part's 64-column
 //               accumulator (one of four);
-//   warps 2-9   epilogue: Y from tensor memory (16 electrons per warp), the
+//   warps 2-5   epilogue, one per lane quarter: Y from tensor memory, the
 //               weights of the lane's union row, the reductions;
-//   warps 10-13 the part's electron geometry (with its 1-D B-spline factors
-//               for the epilogue) and the c' tiles (8 orbitals per K group,
-//               lane = electron).
+//   warps 6-13  the part's electron geometry (with its 1-D B-spline factors
+//               for the epilogue) and the c' tiles (two K groups of 8
+//               orbitals per warp, lane = electron).
 // Every wait is bounded (about 2 s); on a timeout every role winds down as in
 // the evaluation kernel.
 #include <cuda.h>
@@ -58,16 +58,16 @@ namespace blip {
 
 namespace {
 
-constexpr int kRStages = 3;                     // table tile stages (32 KB)
+constexpr int kRStages = 4;                     // table tile stages (32 KB)
 constexpr int kRBSlots = 4;                     // c' tile slots
 constexpr uint32_t kRKG = 64 * 16;              // one K group of a c' tile: 64 rows x 16 B
 constexpr uint32_t kRB = 16 * kRKG;             // one c' tile: 128 orbitals (16 KB)
 constexpr int kRAcc = 4;                        // accumulators
 constexpr int kRAccCols = 64;                   // hi and lo c' columns of 32 electrons
 constexpr uint32_t kRTmemCols = 256;
-constexpr int kCSlots = 2;                      // staged column segments: slots
-constexpr uint32_t kCRow = 512 + 16;            // one electron's 128 orbitals, padded (banks)
-constexpr uint32_t kCSlot = 32 * kCRow;
+constexpr int kREpi = 4;                        // epilogue warps (one per lane quarter)
+constexpr int kRC = 8;                          // operand warps (2 K groups of a tile each)
+static_assert(2 + kREpi + kRC == kThreads / 32, "the ratio kernel's roles fill the block");
 
 struct __align__(16) RPart {
     int cnt;            // electrons, or -1 for "no more parts"
@@ -80,7 +80,7 @@ struct __align__(16) RPart {
 
 constexpr size_t ratio_tc_smem()
 {
-    return kRStages * kStage + kRBSlots * kRB + kCSlots * kCSlot + 2 * sizeof(RPart) +
+    return kRStages * kStage + kRBSlots * kRB + 2 * sizeof(RPart) +
            2 * 4 * 32 * 5 * sizeof(float) + 512;
 }
 
@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     unsigned char *stageA = smem;
     unsigned char *bring = smem + kRStages * kStage;
-    unsigned char *cst = bring + kRBSlots * kRB;                 // staged column segments
-    RPart *info = reinterpret_cast<RPart *>(cst + kCSlots * kCSlot);
+    RPart *info = reinterpret_cast<RPart *>(bring + kRBSlots * kRB);
     float *qsum = reinterpret_cast<float *>(info + 2);          // [2][4 quarters][32][5]
     uint64_t *bars = reinterpret_cast<uint64_t *>(qsum + 2 * 4 * 32 * 5);
     uint64_t *a_full = bars, *a_empty = a_full + kRStages;
@@ -108,8 +107,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *acc_full = epi_done + 2, *acc_empty = acc_full + kRAcc;
     uint64_t *red_done = acc_empty + kRAcc, *drain = red_done + 2;
     uint64_t *cq_full = drain + 1, *cq_empty = cq_full + kColQ;
-    uint64_t *c_full = cq_empty + kColQ, *c_empty = c_full + kCSlots;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(c_empty + kCSlots);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cq_empty + kColQ);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *colq = abort_flag + 1;
     volatile int *decision = colq + kColQ;
@@ -123,28 +121,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(a_empty + s, 1);
         }
         for (int s = 0; s < kRBSlots; ++s) {
-            mbar_init(b_full + s, 4);                // the four operand warps
+            mbar_init(b_full + s, kRC);              // the operand warps
             mbar_init(b_empty + s, 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(w_full + b, 1);
             mbar_init(w_empty + b, 1);
-            mbar_init(epi_done + b, kEpiWarps);
-            mbar_init(red_done + b, 32 * kEpiWarps);
+            mbar_init(epi_done + b, kREpi);
+            mbar_init(red_done + b, 32 * kREpi);
         }
         for (int b = 0; b < kRAcc; ++b) {
             mbar_init(acc_full + b, 1);
-            mbar_init(acc_empty + b, kEpiWarps);
+            mbar_init(acc_empty + b, kREpi);
         }
         mbar_init(drain, 1);
         for (int q = 0; q < kColQ; ++q) {
             mbar_init(cq_full + q, 1);
-            mbar_init(cq_empty + q, 4);
+            mbar_init(cq_empty + q, kRC);
         }
-        for (int q = 0; q < kCSlots; ++q) {
-            mbar_init(c_full + q, 1);
-            mbar_init(c_empty + q, 4);               // the four operand warps
-        }
+
 
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -163,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         // ---------------- columns and TMA producer ----------------
-        long long fill = 0, cfill = 0;
+        long long fill = 0;
         bool ok = true;
         // stage layout (K-major A): stencil column c = 4 kx + ky at c KB,
         // component half h at h 16 KB (one 128-byte-swizzled 8-row atom each)
@@ -229,29 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ends_init(a, k0, n3, lane, ends);
             int z0, s0, cnt;
             while (ok && next_part(a, n3, lane, ends, cur, z0, s0, cnt)) {
-                const int e = lane < cnt ? p.perm[s0 + lane] : 0;
                 for (int m = 0; m < a.mt && ok; ++m) {
-                    if (a.staged) {
-                        // this tile's 128-orbital segment of every electron's
-                        // column, one bulk copy per electron
-                        const int cs = (int)(cfill % kCSlots);
-                        if (cfill >= kCSlots) {
-                            const bool got = wait_bar(c_empty + cs, (unsigned)(((cfill / kCSlots) - 1) & 1),
-                                                      abort_flag);
-                            if (!__all_sync(FULL, got)) {
-                                if (lane == 0) raise_abort(p, abort_flag);
-                                ok = false;
-                                break;
-                            }
-                        }
-                        const unsigned seg = 4u * (unsigned)min(kMT, p.Lreal - m * kMT);
-                        if (lane == 0) mbar_expect_tx(c_full + cs, seg * (unsigned)cnt);
-                        __syncwarp();
-                        if (lane < cnt)
-                            bulk_g2s(cst + cs * kCSlot + lane * kCRow,
-                                     a.rcols + (size_t)e * p.Lreal + (size_t)m * kMT, seg, c_full + cs);
-                        ++cfill;
-                    }
                     for (int pl = 0; pl < APL; ++pl) {
                         const int s = (int)(fill % kRStages);
                         const long long k = fill / kRStages;
@@ -284,10 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool got = mbar_wait(a_full + (int)(f % kRStages), (unsigned)((f / kRStages) & 1));
             if (!__all_sync(FULL, got) && lane == 0) atomicOr(p.status, BLIP_STATUS_TIMEOUT);
         }
-        for (long long f = cfill > kCSlots ? cfill - kCSlots : 0; f < cfill; ++f) {
-            const bool got = mbar_wait(c_full + (int)(f % kCSlots), (unsigned)((f / kCSlots) & 1));
-            if (!__all_sync(FULL, got) && lane == 0) atomicOr(p.status, BLIP_STATUS_TIMEOUT);
-        }
+
 
     } else if (warp == 1) {
         // ---------------- MMA issue (one thread) ----------------
@@ -366,10 +336,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(drain, 0)) atomicOr(p.status, BLIP_STATUS_TIMEOUT);
         }
         __syncwarp();
-    } else if (warp < 2 + kEpiWarps) {
+    } else if (warp < 2 + kREpi) {
         // ---------------- epilogue ----------------
         const int q = warp & 3;
-        const int half = (warp - 2) >> 2;            // electrons 16 half .. 16 half + 15
         const int et = threadIdx.x - 64;
         // positions without a cell (last sort bucket): NaN ratios
         {
@@ -404,77 +373,84 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            uint32_t yh[16], yl[16];
             const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * kRAccCols);
-            tmem_ld16_nowait(taddr + 16 * half, yh);
-            tmem_ld16_nowait(taddr + 32 + 16 * half, yl);
-            tmem_wait_ld();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty + ab);
-            if (++ab == kRAcc) {
-                ab = 0;
-                ab_ph ^= 1;
-            }
-            // two groups of 8 electrons: the weights of this row times Y,
-            // then over the 32 lanes (lane L ends with electron L / 4 of the
-            // group after the butterfly)
             float *qs = qsum + wi * (4 * 32 * 5) + q * (32 * 5);
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {   // electrons 16 half .. 16 half + 15
+                uint32_t yh[16], yl[16];
+                tmem_ld16_nowait(taddr + 16 * half, yh);
+                tmem_ld16_nowait(taddr + 32 + 16 * half, yl);
+                tmem_wait_ld();
+                if (half == 1) {
+                    // both halves are in registers: the accumulator is free
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(acc_empty + ab);
+                    if (++ab == kRAcc) {
+                        ab = 0;
+                        ab_ph ^= 1;
+                    }
+                }
+                // two groups of 8 electrons: the weights of this row times Y,
+                // then over the 32 lanes (lane L ends with electron L / 4 of the
+                // group after the butterfly)
 #pragma unroll
-            for (int grp = 0; grp < 2; ++grp) {
-                float pv[5][8];
+                for (int grp = 0; grp < 2; ++grp) {
+
+                    float pv[5][8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = 16 * half + 8 * grp + u;
-                    const float yv = __uint_as_float(yh[8 * grp + u]) + __uint_as_float(yl[8 * grp + u]);
-                    float w[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-                    if (j < cnt) {
-                        const int kz = r - info[wi].cz[j];
-                        if (kz >= 0 && kz <= 3) {
-                            // the weights of site (kx, ky, kz), as site_weights forms them
-                            const float *f = info[wi].fac[j];
-                            const float X0 = f[3 * kx], X1 = f[3 * kx + 1], X2 = f[3 * kx + 2];
-                            const float Y0 = f[12 + 3 * ky], Y1 = f[13 + 3 * ky], Y2 = f[14 + 3 * ky];
-                            const float Z0 = f[24 + 3 * kz], Z1 = f[25 + 3 * kz], Z2 = f[26 + 3 * kz];
-                            const float *J = p.geo.J, *M = p.geo.M;
-                            const float nrm = p.geo.norm;
-                            const float gx = X1 * Y0 * Z0, gy = X0 * Y1 * Z0, gz = X0 * Y0 * Z1;
-                            const float hxx = X2 * Y0 * Z0, hyy = X0 * Y2 * Z0, hzz = X0 * Y0 * Z2;
-                            const float hxy = X1 * Y1 * Z0, hxz = X1 * Y0 * Z1, hyz = X0 * Y1 * Z1;
-                            w[0] = nrm * (X0 * Y0 * Z0);
-                            w[1] = nrm * (J[0] * gx + J[3] * gy + J[6] * gz);
-                            w[2] = nrm * (J[1] * gx + J[4] * gy + J[7] * gz);
-                            w[3] = nrm * (J[2] * gx + J[5] * gy + J[8] * gz);
-                            w[4] = nrm * (M[0] * hxx + M[1] * hyy + M[2] * hzz +
-                                          2.0f * (M[3] * hxy + M[4] * hxz + M[5] * hyz));
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = 16 * half + 8 * grp + u;
+                        const float yv = __uint_as_float(yh[8 * grp + u]) + __uint_as_float(yl[8 * grp + u]);
+                        float w[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                        if (j < cnt) {
+                            const int kz = r - info[wi].cz[j];
+                            if (kz >= 0 && kz <= 3) {
+                                // the weights of site (kx, ky, kz), as site_weights forms them
+                                const float *f = info[wi].fac[j];
+                                const float X0 = f[3 * kx], X1 = f[3 * kx + 1], X2 = f[3 * kx + 2];
+                                const float Y0 = f[12 + 3 * ky], Y1 = f[13 + 3 * ky], Y2 = f[14 + 3 * ky];
+                                const float Z0 = f[24 + 3 * kz], Z1 = f[25 + 3 * kz], Z2 = f[26 + 3 * kz];
+                                const float *J = p.geo.J, *M = p.geo.M;
+                                const float nrm = p.geo.norm;
+                                const float gx = X1 * Y0 * Z0, gy = X0 * Y1 * Z0, gz = X0 * Y0 * Z1;
+                                const float hxx = X2 * Y0 * Z0, hyy = X0 * Y2 * Z0, hzz = X0 * Y0 * Z2;
+                                const float hxy = X1 * Y1 * Z0, hxz = X1 * Y0 * Z1, hyz = X0 * Y1 * Z1;
+                                w[0] = nrm * (X0 * Y0 * Z0);
+                                w[1] = nrm * (J[0] * gx + J[3] * gy + J[6] * gz);
+                                w[2] = nrm * (J[1] * gx + J[4] * gy + J[7] * gz);
+                                w[3] = nrm * (J[2] * gx + J[5] * gy + J[8] * gz);
+                                w[4] = nrm * (M[0] * hxx + M[1] * hyy + M[2] * hzz +
+                                              2.0f * (M[3] * hxy + M[4] * hxz + M[5] * hyz));
+                            }
                         }
+#pragma unroll
+                        for (int o = 0; o < 5; ++o) pv[o][u] = w[o] * yv;
                     }
 #pragma unroll
-                    for (int o = 0; o < 5; ++o) pv[o][u] = w[o] * yv;
-                }
+                    for (int o = 0; o < 5; ++o) {
 #pragma unroll
-                for (int o = 0; o < 5; ++o) {
+                        for (int st = 0; st < 3; ++st) {
+                            const int off = 16 >> st, hh = 4 >> st;
+                            const bool up = (lane & off) != 0;
 #pragma unroll
-                    for (int st = 0; st < 3; ++st) {
-                        const int off = 16 >> st, hh = 4 >> st;
-                        const bool up = (lane & off) != 0;
-#pragma unroll
-                        for (int i = 0; i < hh; ++i) {
-                            const float send = up ? pv[o][i] : pv[o][i + hh];
-                            const float keep = up ? pv[o][i + hh] : pv[o][i];
-                            pv[o][i] = keep + __shfl_xor_sync(FULL, send, off);
+                            for (int i = 0; i < hh; ++i) {
+                                const float send = up ? pv[o][i] : pv[o][i + hh];
+                                const float keep = up ? pv[o][i + hh] : pv[o][i];
+                                pv[o][i] = keep + __shfl_xor_sync(FULL, send, off);
+                            }
                         }
+                        pv[o][0] += __shfl_xor_sync(FULL, pv[o][0], 2);
+                        pv[o][0] += __shfl_xor_sync(FULL, pv[o][0], 1);
                     }
-                    pv[o][0] += __shfl_xor_sync(FULL, pv[o][0], 2);
-                    pv[o][0] += __shfl_xor_sync(FULL, pv[o][0], 1);
-                }
-                if ((lane & 3) == 0) {
-                    const int j = 16 * half + 8 * grp + (lane >> 2);
+                    if ((lane & 3) == 0) {
+                        const int j = 16 * half + 8 * grp + (lane >> 2);
 #pragma unroll
-                    for (int o = 0; o < 5; ++o) qs[j * 5 + o] = pv[o][0];
+                        for (int o = 0; o < 5; ++o) qs[j * 5 + o] = pv[o][0];
+                    }
                 }
             }
-            mbar_arrive(red_done + wi);                  // all 32 kEpiWarps threads
+            mbar_arrive(red_done + wi);                  // all 32 kREpi threads
             if (!wait_bar(red_done + wi, ph, abort_flag)) {
                 if (lane == 0) raise_abort(p, abort_flag);
                 break;
@@ -490,12 +466,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ---------------- electron geometry and c' tiles ----------------
-        const int ww = warp - 2 - kEpiWarps;
+        const int ww = warp - 2 - kREpi;
         const size_t L = (size_t)p.Lreal;
         // 16-byte loads of the columns when every row starts 16-byte aligned
         const bool vec = (p.Lreal & 3) == 0 && (reinterpret_cast<uintptr_t>(a.rcols) & 15u) == 0;
         bool ok = true;
-        int part = 0, bs = 0, bs_ph = 0, built = 0, cs = 0, cs_ph = 0;
+        int part = 0, bs = 0, bs_ph = 0, built = 0;
         auto claim = [&]() -> bool {
             const int wi = part & 1;
             bool got = true;
@@ -507,9 +483,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!__all_sync(FULL, got) && lane == 0) raise_abort(p, abort_flag);
             // one thread reads the abort flag between two barriers, so the four
             // warps take the same decision (and meet the same barriers after it)
-            named_sync(1, 128);
+            named_sync(1, 32 * kRC);
             if (ww == 0 && lane == 0) *decision = *abort_flag;
-            named_sync(1, 128);
+            named_sync(1, 32 * kRC);
             return !*decision;
         };
         int taken = 0;
@@ -554,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ne = lane < ncnt ? p.perm[ns0 + lane] : 0;
             if (lane < ncnt) {
                 const float *row = a.rcols + (size_t)ne * L;
-                for (int l = 32 * ww; l < p.Lreal; l += 128)
+                for (int l = 32 * ww; l < p.Lreal; l += 32 * kRC)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(row + l));
             }
             return true;
@@ -615,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float rsig = 1.0f / sig;                   // a power of two: exact
             if (ww == 0 && lane == 0) info[wi].cnt = cnt;
             __syncwarp();
-            named_sync(1, 128);
+            named_sync(1, 32 * kRC);
             if (ww == 0 && lane == 0) mbar_arrive(w_full + wi);
             // c' tiles: warp ww the K groups 4 ww .. 4 ww + 3 (orbitals
             // 32 ww .. 32 ww + 31 of the tile); row j hi, row 32 + j lo
@@ -627,38 +603,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 unsigned char *tile = bring + bs * kRB;
-                // the lane's 32 orbitals of the tile (K groups 4 ww .. 4 ww + 3)
-                // and their scales: from the staged segments, or from global
-                // memory with all loads issued before any use
-                const int lb = m * kMT + 32 * ww;
-                float v[32], sv[32];
-                if (a.staged) {
-                    if (!__all_sync(FULL, wait_bar(c_full + cs, (unsigned)cs_ph, abort_flag))) {
-                        if (lane == 0) raise_abort(p, abort_flag);
-                        ok = false;
-                        break;
-                    }
-                    const float4 *src = reinterpret_cast<const float4 *>(cst + cs * kCSlot + j * kCRow) + 8 * ww;
+                // the lane's 16 orbitals of the tile (K groups 2 ww, 2 ww + 1)
+                // and their scales, all loads issued before any use (the
+                // column segments were asked into L2 a part ahead)
+                const int lb = m * kMT + 16 * ww;
+                float v[16], sv[16];
+                if (vec && lb + 16 <= p.Lreal) {
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const float4 c4 = j < cnt ? src[u] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                        v[4 * u] = c4.x; v[4 * u + 1] = c4.y; v[4 * u + 2] = c4.z; v[4 * u + 3] = c4.w;
-                    }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(c_empty + cs);
-                    if (++cs == kCSlots) {
-                        cs = 0;
-                        cs_ph ^= 1;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        // past the last orbital: stale bytes of the slot
-                        if (lb + u >= p.Lreal) v[u] = 0.0f;
-                        sv[u] = (p.scales && lb + u < p.Lreal) ? __ldg(p.scales + lb + u) : 1.0f;
-                    }
-                } else if (vec && lb + 32 <= p.Lreal) {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < 4; ++u) {
                         const float4 c4 = j < cnt ? __ldcs(reinterpret_cast<const float4 *>(crow + lb) + u)
                                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                         const float4 s4 = p.scales ? __ldg(reinterpret_cast<const float4 *>(p.scales + lb) + u)
@@ -668,15 +620,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 } else {
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) {
+                    for (int u = 0; u < 16; ++u) {
                         const int l = lb + u;
                         v[u] = (j < cnt && l < p.Lreal) ? __ldcs(crow + l) : 0.0f;
                         sv[u] = (p.scales && l < p.Lreal) ? __ldg(p.scales + l) : 1.0f;
                     }
                 }
 #pragma unroll
-                for (int gg = 0; gg < 4; ++gg) {
-                    const int g = 4 * ww + gg;
+                for (int gg = 0; gg < 2; ++gg) {
+                    const int g = 2 * ww + gg;
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int u = 0; u < 8; u += 2) {
@@ -784,7 +736,9 @@ cudaError_t launch_ratio_tc_t(const EvalParams &p, const TcArgs &a, const CUtens
     if (!std::is_same<T, __nv_bfloat16>::value) {
         const long long blocks = std::min<long long>(((long long)p.n_elec + 7) / 8, 65535LL * 16);
         ratio_sigma_kernel<<<(unsigned)std::max<long long>(1, blocks), 256, 0, stream>>>(
-            a.rcols, p.n_elec, p.Lreal, p.scales, a.staged, const_cast<float *>(a.rsig));
+            a.rcols, p.n_elec, p.Lreal, p.scales,
+            (p.Lreal % 4) == 0 && (reinterpret_cast<uintptr_t>(a.rcols) & 15u) == 0,
+            const_cast<float *>(a.rsig));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -815,8 +769,6 @@ cudaError_t launch_ratio_tc(const EvalParams &p, int elem, const int *cell_end, 
     a.rcols = rcols;
     a.ratio = ratio;
     a.rsig = sig;
-    // segments staged by bulk copies need 16-byte aligned rows
-    a.staged = (p.Lreal % 4) == 0 && (reinterpret_cast<uintptr_t>(rcols) & 15u) == 0;
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(&tmap);
     const CUtensorMap &tm5k = *reinterpret_cast<const CUtensorMap *>(tmap5k ? tmap5k : &tmap);
     switch (elem) {

@@ -42,7 +42,6 @@ struct TcArgs {
     int *col_ctr;          // work queue: the next column to take (0 at launch)
     const float *rcols;    // ratio mode: [n_elec][Lreal] inverse columns, else null
     const float *rsig;     // ratio kernel: per-electron scale of the column operand, or null
-    int staged;            // ratio kernel: 1 = column segments staged by bulk copies
     float *ratio;          // ratio mode: [n_elec][5] output, else null
 };
 
