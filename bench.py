@@ -83,6 +83,9 @@ def parse():
                     help="override the orbital count (smaller profiling cases)")
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--kernel", default="auto", help="auto | variant,chunks,warps,sort")
+    ap.add_argument("--step", default="eval", choices=["eval", "ratio"],
+                    help="the timed step: the evaluation (blip_eval) or the fused ratio "
+                         "(blip_eval_ratio, cell order, seeded N(0,1) inverse columns)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
@@ -124,6 +127,9 @@ def describe(w, args, E):
          "positions": "uniform in cell" if w.uniform_n else "walker configs + N(0,0.3^2) moves"}
     if args.slab > 0:
         d["slab"] = f"electrons with fractional a_1 coordinate below {args.slab} only"
+    if getattr(args, "step", "eval") == "ratio":
+        d["step"] = ("blip_eval_ratio in cell order: sum_l {psi, grad, lap}_l c_j[l] with "
+                     "seeded N(0,1) columns c_j (5 floats per electron out)")
     return d
 
 
@@ -584,7 +590,13 @@ def main():
     doffs = torch.from_numpy(offs).cuda()
     out = t.alloc_outputs(E)
     stream = torch.cuda.current_stream()
-    if args.kernel == "auto":
+    if args.step == "ratio":
+        # the ratio picks its kernel by density (tensor cores for dense batches)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(7)
+        cols = torch.randn((E, Lr), generator=g, device="cuda", dtype=torch.float32)
+        chosen = (12, 1, 1, 1) if 2 * E >= int(np.prod(w.grid)) else (0, 0, 0, 1)
+    elif args.kernel == "auto":
         chosen = t.autotune(dpos, doffs, out=out)
     else:
         v_, c_, w_, s_ = (int(x) for x in args.kernel.split(","))
@@ -593,7 +605,10 @@ def main():
     st_ = Stepper(args.warm, stream)
 
     def step():
-        t.eval(dpos, doffs, out=out)
+        if args.step == "ratio":
+            t.eval_ratio(dpos, cols, doffs, sort=1)
+        else:
+            t.eval(dpos, doffs, out=out)
 
     for k in range(max(3, args.warmup)):
         st_.flush_l2(k)
@@ -631,10 +646,11 @@ def main():
     # roofline of the evaluation kernel (the dominant kernel of the step)
     U = touched_sites(w.grid, w.lattice, pos)
     b_c = ELEM_BYTES[args.storage]
-    bytes_alg, flops = launch_model("full", E, Lr, U, b_c)
+    bytes_alg, flops = launch_model("ratio" if args.step == "ratio" else "full", E, Lr, U, b_c)
     roof = roofline(bytes_alg, flops, ms, sms, tensor_products(chosen, args.storage))
     kh = kernel_hash()
-    roof["traffic"] = NCU_TRAFFIC.get((kh, w.name, args.storage, E), {}).get(tuple(chosen[:2]))
+    roof["traffic"] = NCU_TRAFFIC.get((kh, w.name, args.storage, E), {}).get(tuple(chosen[:2])) \
+        if args.step == "eval" else None
     roof.update({"touched_sites": U, "kernel_source_hash": kh,
                  "gather_model_GBps": (E * 64 * Lr * b_c + 20 * Lr * E) / (ms / 1e3) / 1e9})
     if not args.no_probe and roof["bound"] == "hbm" and E * Lr * 20 > 4e9:
