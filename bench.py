@@ -834,6 +834,13 @@ def extras_precision(args, pb, w, tab, pos, dpos, doffs, t32, out, st_, line, sm
             ent = _timed_entry(st_.time(lambda: t.eval(db, dob, out=ob_), K), Eb, Lr, Ub,
                                ELEM_BYTES[storage], "full", sms, ch, storage)
             ent.update({"b": b, "E": Eb, "storage": storage})
+            # values only (the paper's own GPU workload), autotuned for it
+            ov = (out[0][:Eb], None, None)
+            chv = t.autotune(db, dob, values_only=True, out=ov)
+            vo = _timed_entry(st_.time(lambda: t.eval(db, dob, values_only=True, out=ov),
+                                       max(3, K // 2)), Eb, Lr, Ub, ELEM_BYTES[storage],
+                              "vonly", sms, chv, storage)
+            ent["values_only"] = {k: vo[k] for k in ("us", "evals_per_s", "bound", "frac", "kernel")}
             sweep.append(ent)
     line["batch_sweep"] = sweep
 
