@@ -334,3 +334,57 @@ def test_ratio_tensor_core_operand_kernel(pb, storage):
         assert (np.abs(rw[ok, k] - ref) <= eb).all(), k
     print(f"\nstorage {storage}: worst operand-kernel ratio error / bound {worst:.3g}")
     assert t.status() == pb.STATUS_NONFINITE_POS
+
+
+@pytest.mark.parametrize("storage,n,misalign", [("f32", 130, False), ("bf16", 300, True)])
+def test_ratio_operand_kernel_scalar_paths(pb, storage, n, misalign):
+    """The ratio kernel's paths without 16-byte column loads: an orbital
+    count that is not a multiple of 4 (130: a ragged second orbital tile),
+    and columns whose base address is 4 bytes off 16-byte alignment.  Both
+    against the FP64 oracle under the operand kernel's bound."""
+    grid = (10, 9, 12)
+    lat = pins.triclinic_lattice()
+    tab = bi.smooth_random_table(grid, n, seed=65, sigma=2.0)
+    rng = np.random.default_rng(66)
+    pos = rng.uniform(0, 1, size=(3 * int(np.prod(grid)), 3)) @ lat
+    E = len(pos)
+    cols = (rng.normal(0.0, 1.0, size=(E, n)) *
+            10.0 ** rng.uniform(-2, 2, size=(E, 1))).astype(np.float32)
+    kind = pb.F32 if storage == "f32" else pb.BF16
+    t = pb.BlipTable(grid, lat, tab, storage=kind)
+    if misalign:
+        buf = torch.empty(E * n + 1, dtype=torch.float32, device="cuda")
+        dcols = buf[1:].view(E, n)
+        dcols.copy_(torch.from_numpy(cols))
+        assert dcols.data_ptr() % 16 != 0
+    else:
+        dcols = torch.from_numpy(cols).cuda()
+    r, _ = t.eval_ratio(torch.from_numpy(pos).cuda(), dcols, sort=1)
+    torch.cuda.synchronize()
+    r = r.cpu().numpy().astype(np.float64)
+    rv, rg, rl, mag = oracle.eval_stencil(grid, lat, tab, pos, absmag=True)
+    c64 = cols.astype(np.float64)
+    outs = [rv, rg[:, 0], rg[:, 1], rg[:, 2], rl]
+    u_q = {"f32": 0.0, "bf16": 2.0 ** -8}[storage]
+    amax = np.abs(tab.reshape(-1, n)).max(0)
+    s_l = 2.0 ** np.ceil(np.log2(amax)) if storage == "f32" else amax
+    floor = np.zeros((E, 5, n))
+    if storage == "f32":
+        ones = np.ones(tuple(grid) + (1,))
+        _, _, _, sw = oracle.eval_stencil(grid, lat, ones, pos, absmag=True)
+        floor = 2.0 ** -25 * (64.0 + sw[:, :, 0])[:, :, None] * (2.0 * amax)[None, None, :]
+    sig = 2.0 ** np.ceil(np.log2(np.abs(c64 * s_l[None, :]).max(1)))
+    mt = (n + 127) // 128
+    for k in range(5):
+        ref = (outs[k] * c64).sum(1)
+        summ = 2 * (n / 32 + 8) * 2.0 ** -24 * np.abs(outs[k] * c64).sum(1)
+        base = (np.abs(c64) * ((1.6e-5 + u_q) * mag[:, k] + floor[:, k])).sum(1)
+        acc = (16 * mt + 16) * 2.0 ** -24 * (np.abs(c64) * mag[:, k]).sum(1)
+        if storage == "bf16":
+            split = 2.0 ** -17 * (np.abs(outs[k]) * np.abs(c64)).sum(1)
+        else:
+            split = (np.abs(outs[k]) * (2.0 ** -22 * np.abs(c64) +
+                                        2.0 ** -25 * sig[:, None] / s_l[None, :])).sum(1)
+        bound = base + acc + split + summ + 1e-30
+        assert (np.abs(r[:, k] - ref) <= bound).all(), (k, float((np.abs(r[:, k] - ref) / bound).max()))
+    assert t.status() == 0
