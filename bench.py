@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     # tensor-core kernel: captured on the electrons of a slab (a_1 < 1/8) of
     # the batch at the same density (196,327 electrons), scaled by electrons
     # to the full batch (outputs dominate: traffic grows in proportion)
-    ("39844389e3b7b26a", "tio2_precision", "f32", 1572864): {
+    ("fbf8723eb9be50ef", "tio2_precision", "f32", 1572864): {
         (12, 1): (321207552 + 2954819072) * 1572864 // 196327},
 }
 
@@ -161,14 +161,19 @@ def _code_only(text):
     return " ".join(text.split())
 
 
+# sources outside the evaluation path: the Sherman-Morrison update and the
+# two fused-ratio kernels
+_NOT_EVAL_PATH = ("blip_sm.cu", "blip_ratio.cu", "blip_ratio_tc.cu")
+
+
 def kernel_hash():
     """SHA-256 (16 hex digits) of the code (comments aside) of every CUDA
     source of the evaluation path (all of the library but the
-    Sherman-Morrison update)."""
+    Sherman-Morrison update and the fused-ratio kernels)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1204_1121_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")) and f != "blip_sm.cu":
+        if f.endswith((".cu", ".cuh", ".h")) and f not in _NOT_EVAL_PATH:
             with open(os.path.join(csrc, f), encoding="utf-8") as fh:
                 h.update(f.encode() + b"\0" + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]

@@ -64,7 +64,14 @@ def test_kernel_hash_tracks_the_evaluation_sources(tmp_path, monkeypatch):
     f.write_text(text + "\nstatic int unused_probe;\n")
     assert bench.kernel_hash() != h0                   # code does
     f.write_text(text)
-    # the Sherman-Morrison update is not part of the evaluation path
-    g = root / "paper_1204_1121_gb300" / "csrc" / "blip_sm.cu"
+    # the Sherman-Morrison update and the fused-ratio kernels are not part of
+    # the evaluation path
+    for name in ("blip_sm.cu", "blip_ratio.cu", "blip_ratio_tc.cu"):
+        g = root / "paper_1204_1121_gb300" / "csrc" / name
+        g.write_text(g.read_text() + "\nstatic int unused_probe;\n")
+        assert bench.kernel_hash() == h0
+    # the helpers the tensor-core evaluation kernel shares with the ratio
+    # kernel are
+    g = root / "paper_1204_1121_gb300" / "csrc" / "blip_tc_common.cuh"
     g.write_text(g.read_text() + "\nstatic int unused_probe;\n")
-    assert bench.kernel_hash() == h0
+    assert bench.kernel_hash() != h0
