@@ -388,3 +388,58 @@ def test_ratio_operand_kernel_scalar_paths(pb, storage, n, misalign):
         bound = base + acc + split + summ + 1e-30
         assert (np.abs(r[:, k] - ref) <= bound).all(), (k, float((np.abs(r[:, k] - ref) / bound).max()))
     assert t.status() == 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_ratio_tensor_cores_full_precision_batch(pb, storage):
+    """The fused ratio at full size, in the launch configuration bench.py
+    times (1,024 walkers x 1,536 trial moves on the TiO2-shaped table, cell
+    order, no new rows: the operand kernel), with seeded N(0,1) columns made
+    on the device: 48 sampled electrons against the FP64 oracle's
+    contraction under the operand kernel's bound."""
+    w = bi.workload("tio2")
+    tab = w.table()
+    wp = bi.workload("tio2_precision")
+    pos, offs = wp.positions()
+    E, n = len(pos), tab.shape[-1]
+    kind = pb.F32 if storage == "f32" else pb.BF16
+    t = pb.BlipTable(w.grid, w.lattice, tab, storage=kind)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(67)
+    dcols = torch.randn((E, n), generator=g, device="cuda", dtype=torch.float32)
+    r, _ = t.eval_ratio(torch.from_numpy(pos).cuda(), dcols, torch.from_numpy(offs).cuda(), sort=1)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(68)
+    idx = np.unique(np.concatenate([[0, E - 1], rng.integers(0, E, 46)]))
+    got = r[idx].cpu().numpy().astype(np.float64)
+    c64 = dcols[idx].cpu().numpy().astype(np.float64)
+    del dcols
+    rv, rg, rl, mag = oracle.eval_stencil(w.grid, w.lattice, tab, pos[idx], absmag=True)
+    outs = [rv, rg[:, 0], rg[:, 1], rg[:, 2], rl]
+    u_q = {"f32": 0.0, "bf16": 2.0 ** -8}[storage]
+    amax = np.abs(tab.reshape(-1, n)).max(0)
+    s_l = 2.0 ** np.ceil(np.log2(amax)) if storage == "f32" else amax
+    floor = np.zeros((len(idx), 5, n))
+    if storage == "f32":
+        ones = np.ones(tuple(w.grid) + (1,))
+        _, _, _, sw = oracle.eval_stencil(w.grid, w.lattice, ones, pos[idx], absmag=True)
+        floor = 2.0 ** -25 * (64.0 + sw[:, :, 0])[:, :, None] * (2.0 * amax)[None, None, :]
+    sig = 2.0 ** np.ceil(np.log2(np.abs(c64 * s_l[None, :]).max(1)))
+    mt = (n + 127) // 128
+    worst = 0.0
+    for k in range(5):
+        ref = (outs[k] * c64).sum(1)
+        summ = 2 * (n / 32 + 8) * 2.0 ** -24 * np.abs(outs[k] * c64).sum(1)
+        base = (np.abs(c64) * ((1.6e-5 + u_q) * mag[:, k] + floor[:, k])).sum(1)
+        acc = (16 * mt + 16) * 2.0 ** -24 * (np.abs(c64) * mag[:, k]).sum(1)
+        if storage == "bf16":
+            split = 2.0 ** -17 * (np.abs(outs[k]) * np.abs(c64)).sum(1)
+        else:
+            split = (np.abs(outs[k]) * (2.0 ** -22 * np.abs(c64) +
+                                        2.0 ** -25 * sig[:, None] / s_l[None, :])).sum(1)
+        bound = base + acc + split + summ + 1e-30
+        e = np.abs(got[:, k] - ref) / bound
+        worst = max(worst, float(e.max()))
+        assert (e <= 1.0).all(), (k, float(e.max()))
+    print(f"\nstorage {storage}: full-size ratio, worst error / bound {worst:.3g}")
+    assert t.status() == 0
