@@ -319,13 +319,24 @@ int blip_set_kpoints(blip_table t, int n_k, const double *kfrac, const int *koff
  *   values     device [n_elec][n_orb] float for the new rows psi_l(r'_j)
  *              (needed to update D^{-1} after an accepted move), or NULL
  *   sort       0: input order; 1: grid-cell order, and for dense batches
- *              (n_elec >= half the grid cells) the tensor-core kernel
- *              (matrix products over the union rows of up to 25 electrons,
- *              FP32 accumulation; its rounding differs from the CUDA cores'
- *              within the per-output bound 1.6e-5 sum_s |W_o(s)| |a_ls|);
+ *              (n_elec >= half the grid cells) the tensor cores: without
+ *              `values`, the orbital sum first (sum_k W_o[k] sum_l a[k][l]
+ *              inv_cols[j][l] over the union rows k of up to 25 electrons,
+ *              the columns split into two 16-bit parts; for FP32 and FP16
+ *              tables scaled per electron by a power of two from a pre-pass
+ *              over the columns); with `values`, the evaluation kernel's
+ *              products contracted in its epilogue.  Both accumulate in FP32
+ *              and round differently from the CUDA cores, within the
+ *              per-output bound 1.6e-5 sum_s |W_o(s)| |a_ls| carried through
+ *              the column (plus the column's 16-bit split);
  *              2: grid-cell order on the CUDA cores only
+ * The tensor-core path builds its operand planes and tensor maps on first
+ * use, and the per-electron scales of FP32 / FP16 tables need n_elec floats
+ * of scratch, allocated when a larger batch first arrives: make the first
+ * call of a batch size outside stream capture (under capture without them
+ * the call falls back to the CUDA cores or to the epilogue contraction).
  * Other arguments as blip_eval.  Deterministic (fixed reduction order).
- * Errors: INVALID_ARG, UNSUPPORTED_DTYPE (complex tables), CUDA.
+ * Errors: INVALID_ARG, UNSUPPORTED_DTYPE (complex tables), OOM, CUDA.
  */
 int blip_eval_ratio(blip_table t, const double *pos, int n_elec, const int *walker_offsets,
                     int n_walkers, const float *inv_cols, float *ratio, float *values, int sort,
